@@ -1,0 +1,19 @@
+"""Oracle for beta = A alpha: TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, obviously correct CPU implementation of the polynomial basis conversion
+of Townsend, Webb & Olver (arXiv:1604.07486), written from the paper alone.  Only
+tests/, __graft_entry__.smoke() and the CPU-baseline legs of bench.py may import it.
+It shares no code with the CUDA library and the library never imports it.
+
+Parity status: every function here is pinned by -m "not gpu" tests (exact rational
+conversion, Clenshaw evaluation, Hankel moment integrals, L M = I, the K = 27 rank of
+Sec. 2.1, and the full-update Cholesky form), except ``fast_matvec``, which is a CPU
+timing reference and is never used as parity truth.
+"""
+from .oracle import (CHEB2LEG, JAC, LAG, LEG2CHEB, ULTRA, entries, fast_matvec, first_index,
+                     hankel, hankel_factors, jac2jac, lambda_dd, matvec, pivoted_cholesky,
+                     pivoted_cholesky_full, split, threads)
+
+__all__ = ["CHEB2LEG", "JAC", "LAG", "LEG2CHEB", "ULTRA", "entries", "fast_matvec",
+           "first_index", "hankel", "hankel_factors", "jac2jac", "lambda_dd", "matvec",
+           "pivoted_cholesky", "pivoted_cholesky_full", "split", "threads"]

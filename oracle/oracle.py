@@ -1,0 +1,250 @@
+"""Plain CPU oracle for polynomial basis conversion (TEST INFRASTRUCTURE ONLY).
+
+What the CUDA path is checked against.  Only tests/, __graft_entry__.smoke() and the
+CPU-baseline legs of bench.py may import this module; the library never does.
+
+Source: Townsend, Webb & Olver, "Fast polynomial transforms based on Toeplitz and Hankel
+matrices" (arXiv:1604.07486).
+
+* ``matvec`` / ``entries`` / ``split`` wrap the double-double C oracle (tdh_oracle.c):
+  the dense "Direct" product of Sec. 4 with entries from their closed forms.
+* ``pivoted_cholesky`` is the O(K^2 N) algorithm of Sec. 2.1 (Fig. 2), steps in the
+  paper's order, in float64.  Reading of the garbled inner update of Fig. 2: step j is
+  applied to the new column as l_r <- l_r - l_j (l_j)_{p_r} / a_j, which is what the
+  prose of Sec. 2.1 describes (apply each earlier Cholesky step to column p_r).
+* ``pivoted_cholesky_full`` is the O(K N^2) full-update form, eq. (FirstCholeskyStep).
+* ``jac2jac`` composes the Case-2 formula with the reflection of Sec. 5.3 when
+  beta != delta (reading: P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x)).
+* ``fast_matvec`` is the outline of Fig. 1 in float64 with numpy's FFT as the Toeplitz
+  step; it is a CPU timing reference only, never the parity truth.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LEG2CHEB, CHEB2LEG, ULTRA, JAC, LAG = 0, 1, 2, 3, 4
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        i64, dbl_p, i64_p = ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+        lib.tdho_matvec.argtypes = [ctypes.c_int, dbl_p, i64, dbl_p, i64, i64, i64_p, i64, dbl_p,
+                                    i64, ctypes.c_int, ctypes.c_int]
+        lib.tdho_entries.argtypes = [ctypes.c_int, dbl_p, i64, i64, i64, i64, i64, dbl_p]
+        lib.tdho_split.argtypes = [ctypes.c_int, dbl_p, i64, dbl_p, dbl_p, dbl_p, dbl_p]
+        lib.tdho_lambda.argtypes = [i64, dbl_p, dbl_p]
+        lib.tdho_threads.argtypes = []
+        for f in (lib.tdho_matvec, lib.tdho_entries, lib.tdho_split, lib.tdho_lambda, lib.tdho_threads):
+            f.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _params(params):
+    p = np.zeros(4, dtype=np.float64)
+    if params is not None:
+        p[: len(params)] = params
+    return p
+
+
+def threads():
+    """Host threads the dense oracle runs on."""
+    return int(_load().tdho_threads())
+
+
+def matvec(kind, params, x, rows=None, transpose=False, nthreads=0):
+    """beta = A x (or A^T x) for every row in ``rows`` (all rows if None).
+
+    x: float64 array [batch][n] or [n].  Returns float64 [batch][len(rows)] (or 1-D).
+    """
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    squeeze = x.ndim == 1
+    if squeeze:
+        x = x[None, :]
+    batch, n = x.shape
+    p = _params(params)
+    if rows is None:
+        nrows, rows_p = n, None
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        nrows = rows.size
+        rows_p = rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    y = np.zeros((batch, nrows), dtype=np.float64)
+    rc = lib.tdho_matvec(kind, _dp(p), n, _dp(x), batch, n, rows_p, nrows, _dp(y), nrows,
+                         1 if transpose else 0, nthreads)
+    if rc != 0:
+        raise ValueError(f"oracle matvec failed ({rc})")
+    return y[0] if squeeze else y
+
+
+def entries(kind, params, n, j0=0, j1=None, k0=0, k1=None):
+    """Dense block A[j0:j1, k0:k1] from the closed forms (rounded once to float64)."""
+    j1 = n if j1 is None else j1
+    k1 = n if k1 is None else k1
+    out = np.zeros((j1 - j0, k1 - k0), dtype=np.float64)
+    rc = _load().tdho_entries(kind, _dp(_params(params)), n, j0, j1, k0, k1, _dp(out))
+    if rc != 0:
+        raise ValueError(f"oracle entries failed ({rc})")
+    return out
+
+
+def split(kind, params, n):
+    """Generator sequences of A = D1 (T o H) D2: (t[n], h[2n-1], d1[n], d2[n])."""
+    t = np.zeros(n)
+    h = np.zeros(2 * n - 1)
+    d1 = np.zeros(n)
+    d2 = np.zeros(n)
+    rc = _load().tdho_split(kind, _dp(_params(params)), n, _dp(t), _dp(h), _dp(d1), _dp(d2))
+    if rc != 0:
+        raise ValueError(f"oracle split failed ({rc})")
+    return t, h, d1, d2
+
+
+def lambda_dd(count):
+    """Lambda(i/2) = Gamma(i/2 + 1/2)/Gamma(i/2 + 1), i < count, as (hi, lo) double-double."""
+    hi = np.zeros(count)
+    lo = np.zeros(count)
+    _load().tdho_lambda(count, _dp(hi), _dp(lo))
+    return hi, lo
+
+
+def hankel(h, n, j0=0):
+    """Dense Hankel block H[j, k] = h[j + k] for j, k in [j0, n)."""
+    idx = np.arange(j0, n)
+    return h[idx[:, None] + idx[None, :]]
+
+
+def first_index(kind):
+    """Index where the positive semidefinite Hankel block starts (Sec. 5.1: row 0 of
+    Chebyshev-to-Legendre is applied directly)."""
+    return 1 if kind == CHEB2LEG else 0
+
+
+# ---------------------------------------------------------------- pivoted Cholesky
+
+def pivoted_cholesky(column, diag, tol, kmax=None):
+    """Sec. 2.1, Fig. 2: rank-K approximation H ~ sum_r l_r l_r^T / a_r.
+
+    column(p) -> H[:, p] (float64, length N); diag = diag(H).
+    Stops before step r when the pivot is "zero or sufficiently small": max(d) <= tol * d0
+    or the pivot entry a_r = (l_r)_{p_r} of the updated column <= tol * d0, where
+    d0 = max(diag(H)).  (a_r is the diagonal entry of H^(r-1) that d approximates; the
+    two differ only by rounding, and checking both keeps a_r > 0.)
+    Ties in the argmax go to the lowest index.  Returns (ells [K][N], a [K], pivots [K]).
+    """
+    d = np.array(diag, dtype=np.float64, copy=True)
+    N = d.size
+    kmax = N if kmax is None else min(kmax, N)
+    d0 = float(d.max()) if N else 0.0
+    ells, a, piv = [], [], []
+    for _ in range(kmax):
+        p = int(np.argmax(d))
+        if not d[p] > tol * d0:
+            break
+        ell = np.array(column(p), dtype=np.float64, copy=True)
+        for j in range(len(ells)):
+            ell -= ells[j] * (ells[j][p] / a[j])
+        a_r = float(ell[p])
+        if not a_r > tol * d0:
+            break
+        ells.append(ell)
+        a.append(a_r)
+        piv.append(p)
+        d -= ell * ell / a_r
+    return np.array(ells).reshape(len(ells), N), np.array(a), np.array(piv, dtype=np.int64)
+
+
+def pivoted_cholesky_full(H, tol, kmax=None):
+    """eq. (FirstCholeskyStep) applied repeatedly: H^(r) = H^(r-1) - H_{:,p} H_{p,:} / H_pp.
+
+    The O(K N^2) form that updates the whole matrix; same pivot and stop rule as
+    ``pivoted_cholesky``.  Returns (ells, a, pivots) with l_r = H^(r-1)[:, p_r].
+    """
+    R = np.array(H, dtype=np.float64, copy=True)
+    N = R.shape[0]
+    kmax = N if kmax is None else min(kmax, N)
+    d0 = float(np.diag(R).max()) if N else 0.0
+    ells, a, piv = [], [], []
+    for _ in range(kmax):
+        dg = np.diag(R)
+        p = int(np.argmax(dg))
+        if not dg[p] > tol * d0:
+            break
+        col = R[:, p].copy()
+        ells.append(col)
+        a.append(float(col[p]))
+        piv.append(p)
+        R = R - np.outer(col, R[p, :]) / col[p]
+    return np.array(ells).reshape(len(ells), N), np.array(a), np.array(piv, dtype=np.int64)
+
+
+def hankel_factors(kind, params, n, tol, kmax=None):
+    """Pivoted Cholesky of the PSD Hankel part of ``kind`` on indices [j0, n).
+
+    Returns (u [K][n], pivots) with u_r = l_r / sqrt(a_r) zero-extended below j0, so that
+    H[j0:, j0:] ~ sum_r u_r u_r^T.
+    """
+    t, h, d1, d2 = split(kind, params, n)
+    j0 = first_index(kind)
+    idx = np.arange(j0, n)
+    ells, a, piv = pivoted_cholesky(lambda p: h[idx + idx[p]], h[2 * idx], tol, kmax)
+    u = np.zeros((len(a), n))
+    if len(a):
+        u[:, j0:] = ells / np.sqrt(a)[:, None]
+    return u, piv + j0
+
+
+# ---------------------------------------------------------------- compositions
+
+def jac2jac(x, a, b, g, d, rows=None):
+    """Jacobi (a, b) -> (g, d) coefficients.
+
+    beta == delta: the Case-2 formula directly.  Otherwise (Sec. 5.3 reflection):
+    flip signs, convert (b, a) -> (d, a), flip back, then convert (a, d) -> (g, d).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    if b == d:
+        return matvec(JAC, (a, b, g), x, rows=rows)
+    n = x.shape[-1]
+    sign = (-1.0) ** np.arange(n)
+    y = sign * matvec(JAC, (b, a, d), sign * x)
+    return matvec(JAC, (a, d, g), y, rows=rows)
+
+
+# ---------------------------------------------------------------- CPU timing reference
+
+def fast_matvec(kind, params, x, tol=1e-15):
+    """Fig. 1 outline in float64: split, pivoted Cholesky, v = D2 x, w = (T o H) v via
+    eq. (Cdecomposition) with numpy FFT Toeplitz products, beta = D1 w.  Row 0 of
+    Chebyshev-to-Legendre is applied directly (Sec. 5.1).  CPU timing reference only."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    n = x.shape[-1]
+    t, h, d1, d2 = split(kind, params, n)
+    u, _ = hankel_factors(kind, params, n, tol)
+    L = 1
+    while L < 2 * n - 1:
+        L *= 2
+    spec = np.conj(np.fft.rfft(t, L))
+    v = x * d2
+    w = np.zeros_like(v)
+    for ur in u:
+        xr = v * ur
+        y = np.fft.irfft(np.fft.rfft(xr, L, axis=-1) * spec, L, axis=-1)[..., :n]
+        w += ur * y
+    beta = w * d1
+    if kind == CHEB2LEG:
+        beta[:, 0] = matvec(CHEB2LEG, None, x, rows=[0])[:, 0]
+    return beta
