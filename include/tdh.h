@@ -1,0 +1,148 @@
+/*
+ * tdh.h -- C ABI of the GB300 Toeplitz-dot-Hankel polynomial basis conversion library.
+ *
+ * Method: Townsend, Webb & Olver, "Fast polynomial transforms based on Toeplitz and Hankel
+ * matrices" (arXiv:1604.07486).  A conversion matrix is split as A = D1 (T o H) D2 (Fig. 1
+ * step 1, eq. (HadamardDecomposition)); the Hankel part H is compressed by pivoted Cholesky,
+ * H ~ sum_r l_r l_r^T / a_r (Sec. 2.1, Fig. 2); and beta = A alpha is computed as
+ * D1 sum_r D_{u_r} T D_{u_r} D2 alpha with u_r = l_r / sqrt(a_r) (eq. (Cdecomposition)),
+ * each Toeplitz product by FFT (Sec. 1, "O(K) FFTs of size 2N-1").
+ *
+ * Conventions for every entry point
+ *   - Pointers named d_* or documented as "device" are CUDA device pointers on the current
+ *     device; pointers documented as "host" are ordinary host memory.  The library never
+ *     takes ownership of caller memory.
+ *   - Vectors are dense, row-major: vector b of a batch occupies in[b * n .. b * n + n).
+ *     Element k is the coefficient of the degree-k basis polynomial.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously on it unless stated otherwise.
+ *   - Every function returns TDH_OK (0) or a negative TDH_ERR_* code; on error a message is
+ *     available from tdh_last_error() (thread-local) and no output is written unless stated.
+ *   - The library is single-GPU: a plan belongs to the device that was current at creation
+ *     and must be used with that device current.
+ */
+#ifndef TDH_H
+#define TDH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- kinds (basis pairs) */
+#define TDH_LEG2CHEB    0 /* Legendre -> Chebyshev, eq. (M), split eq. (Decomposition)       */
+#define TDH_CHEB2LEG    1 /* Chebyshev -> Legendre, eq. (FormulaL), split Sec. 5.1           */
+#define TDH_ULTRA2ULTRA 2 /* ultraspherical C^(l1) -> C^(l2), Sec. 5.2, p = {l1, l2}          */
+#define TDH_JAC2JAC     3 /* Jacobi P^(a,b) -> P^(g,d), Sec. 5.3, p = {a, b, g, d}           */
+
+/* ---------------------------------------------------------------- execute precisions */
+#define TDH_FP64  0 /* float64 in/out, float64 FFT                                             */
+#define TDH_FP32  1 /* float32 in/out, float32 FFT (plan factors rounded once from float64)    */
+
+/* ---------------------------------------------------------------- plan flags */
+#define TDH_FLAG_NONE 0
+
+/* ---------------------------------------------------------------- error codes */
+#define TDH_OK               0
+#define TDH_ERR_INVALID_ARG (-1) /* bad kind, n < 1, parameter out of range, tol <= 0, NULL  */
+#define TDH_ERR_UNSUPPORTED (-2) /* valid request this build does not implement            */
+#define TDH_ERR_NOMEM       (-3) /* device or host allocation failed                       */
+#define TDH_ERR_ALIGN       (-4) /* pointer not aligned to 16 bytes                         */
+#define TDH_ERR_TIMEOUT     (-5) /* a bounded device wait gave up                           */
+#define TDH_ERR_CUDA        (-6) /* a CUDA runtime call failed (message has the detail)     */
+#define TDH_ERR_ALIAS       (-7) /* out overlaps in where the operation forbids it          */
+
+typedef struct tdh_plan_s* tdh_plan_t; /* opaque; immutable after creation */
+
+typedef struct {
+    double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; ignored otherwise   */
+    int prec;     /* TDH_FP64 or TDH_FP32: the precision of plan_execute's in/out and FFTs  */
+    int flags;    /* TDH_FLAG_* (none defined yet; pass 0)                                  */
+    int64_t kmax; /* cap on the rank of each Hankel factorisation; 0 selects 128            */
+} tdh_params;
+
+/*
+ * tdh_plan_create -- build everything beta = A alpha needs for vectors of n_max coefficients
+ * (degree n_max - 1), on the current device, in float64 (Fig. 1 steps 1-2):
+ *   a1  the split's generator sequences t, h and diagonals D1, D2 from their closed forms
+ *       (Gamma ratios by an asymptotic series at large argument, Tricomi-Erdelyi);
+ *   a2  pivoted Cholesky of H (Sec. 2.1, Fig. 2), stopping before the first pivot a_r with
+ *       a_r <= tol * max(diag H) ("zero or sufficiently small"), at most kmax steps;
+ *   a3  the spectrum of the Toeplitz symbol for each FFT length in use.
+ * For TDH_CHEB2LEG the factorisation covers indices 1..n_max-1 and row 0 is applied directly
+ * (Sec. 5.1).  tol > 0 is relative to the largest diagonal entry of H; the paper takes
+ * "a small multiple of machine epsilon" of the arithmetic used.
+ * Synchronous: returns after the plan is complete.  *out receives the handle.
+ * Errors: INVALID_ARG (kind, n_max < 1, tol <= 0, NULL out/params, parameters outside the
+ * supported case), UNSUPPORTED (a case this build lacks), NOMEM, CUDA.
+ */
+int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double tol,
+                    tdh_plan_t* out);
+
+/*
+ * tdh_plan_execute -- beta = A alpha for `batch` vectors of n_max coefficients (Fig. 1 steps
+ * 3-5): v = D2 alpha, w = sum_r u_r o T (u_r o v), beta = D1 w (+ row 0 for Cheb->Leg).
+ * in:  device, batch * n_max values of the plan's precision (float64 or float32).
+ * out: device, same shape and type; must not overlap `in` (TDH_ERR_ALIAS).
+ * Both pointers 16-byte aligned (TDH_ERR_ALIGN).  batch == 0 is a no-op.
+ * Asynchronous on `stream`; the plan may be used from several streams at once.
+ */
+int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream);
+
+/*
+ * tdh_plan_execute_adjoint -- grad = A^T g for `batch` vectors (the transpose product used
+ * by reverse-mode differentiation): A^T = D2 (T^T o H) D1 with H symmetric, so the same
+ * factors serve and T^T is applied with the conjugate (reversed) symbol.
+ * Same layout, alignment, aliasing and stream rules as tdh_plan_execute.
+ */
+int tdh_plan_execute_adjoint(tdh_plan_t plan, const void* in, void* out, int64_t batch,
+                             void* stream);
+
+/*
+ * tdh_plan_query -- report the plan's rank and size.  K (host, may be NULL) receives the
+ * largest rank over the plan's conversion steps; n_max (host, may be NULL) its length.
+ */
+int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max);
+
+/* tdh_plan_destroy -- free the plan's device and host memory.  NULL is a no-op.  Waits for
+ * nothing: the caller must not destroy a plan with launches still in flight. */
+int tdh_plan_destroy(tdh_plan_t plan);
+
+/* tdh_last_error -- message of the last failing call on this thread ("" if none). */
+const char* tdh_last_error(void);
+
+/*
+ * tdh_symbols -- step a1 on its own: the split A = D1 (T o H) D2 of `kind` for n
+ * coefficients, in float64, written to device arrays
+ *   t[n]       T_{j, j+m} = t[m]           (upper-triangular Toeplitz generator)
+ *   h[2n-1]    H_{jk} = h[j + k]           (Hankel generator)
+ *   d1[n], d2[n]                            (the diagonals)
+ * following eq. (Decomposition) (LEG2CHEB), Sec. 5.1 (CHEB2LEG; h[0] = 1), Sec. 5.2 (ULTRA,
+ * Case 2, |l1 - l2| < 1) and Sec. 5.3 (JAC with b == d, Case 2).  p as in tdh_params.p.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ */
+int tdh_symbols(int kind, int64_t n, const double* p, double* t, double* h, double* d1,
+                double* d2, void* stream);
+
+/*
+ * tdh_pchol -- step a2 on its own: pivoted Cholesky (Sec. 2.1, Fig. 2) of the positive
+ * semidefinite Hankel block H[j, k] = h[j + k], j, k in [j0, n), in float64.
+ *   h       device, 2n - 1 values.
+ *   u       device, kmax * n values (row-major [kmax][n]); row r receives
+ *           u_r = l_r / sqrt(a_r) (zero below j0), so that H ~ sum_r u_r u_r^T.
+ *   pivots  device, kmax int64 values; pivot index p_r (in [j0, n)) of step r.
+ *   K       host; receives the number of steps taken.
+ * Step r picks p_r = argmax d (lowest index on ties), forms column p_r of H minus the
+ * earlier steps applied to it, and stops before any pivot a_r <= tol * max(diag H).
+ * Synchronous (reads K back).  Errors: INVALID_ARG (n < 1, j0 not 0/1, tol <= 0,
+ * kmax < 1), NOMEM, CUDA.
+ */
+int tdh_pchol(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, double* u,
+              int64_t* pivots, int64_t* K, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TDH_H */

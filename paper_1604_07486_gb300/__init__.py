@@ -1,0 +1,183 @@
+"""GB300 Toeplitz-dot-Hankel polynomial basis conversion (Townsend, Webb & Olver,
+arXiv:1604.07486): beta = A alpha with A = D1 (T o H) D2, H compressed by pivoted Cholesky,
+each Toeplitz product by FFT -- all in the CUDA library libtdh.so (include/tdh.h).
+
+This module only marshals arguments to that C ABI.  PyTorch supplies device memory and
+streams; every step of the conversion runs in the library's kernels.  There is no CPU
+fallback: if the library is not built or no GPU is present, calls raise.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+LEG2CHEB, CHEB2LEG, ULTRA2ULTRA, JAC2JAC = 0, 1, 2, 3
+FP64, FP32 = 0, 1
+KINDS = {"leg2cheb": LEG2CHEB, "cheb2leg": CHEB2LEG, "ultra2ultra": ULTRA2ULTRA,
+         "jac2jac": JAC2JAC}
+PRECS = {"fp64": FP64, "fp32": FP32}
+ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "NOMEM", -4: "ALIGN",
+          -5: "TIMEOUT", -6: "CUDA", -7: "ALIAS"}
+
+# Every entry point include/tdh.h declares (checked by the CPU test suite).
+EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "tdh_plan_query",
+           "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol")
+
+
+class TdhError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_double * 4), ("prec", ctypes.c_int), ("flags", ctypes.c_int),
+                ("kmax", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libtdh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built ({path}); call "
+                               "paper_1604_07486_gb300.build.build() first")
+        L = ctypes.CDLL(path)
+        vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        L.tdh_plan_create.argtypes = [ctypes.c_int, i64, ctypes.POINTER(_Params), dbl,
+                                      ctypes.POINTER(vp)]
+        L.tdh_plan_execute.argtypes = [vp, vp, vp, i64, vp]
+        L.tdh_plan_execute_adjoint.argtypes = [vp, vp, vp, i64, vp]
+        L.tdh_plan_query.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.tdh_plan_destroy.argtypes = [vp]
+        L.tdh_last_error.argtypes = []
+        L.tdh_last_error.restype = ctypes.c_char_p
+        L.tdh_symbols.argtypes = [ctypes.c_int, i64, ctypes.POINTER(dbl), vp, vp, vp, vp, vp]
+        L.tdh_pchol.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
+        for name in EXPORTS:
+            if name != "tdh_last_error":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise TdhError(rc, lib().tdh_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _kind(kind):
+    return KINDS[kind] if isinstance(kind, str) else int(kind)
+
+
+class Plan:
+    """A conversion plan (tdh_plan_create): symbols, pivoted Cholesky and FFT tables for
+    vectors of n coefficients, built on the current CUDA device in float64."""
+
+    def __init__(self, kind, n, prec="fp32", tol=None, params=(), kmax=0):
+        self.kind = _kind(kind)
+        self.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
+        if tol is None:
+            tol = 1e-15 if self.prec == FP64 else 1e-7
+        p = _Params()
+        for i, v in enumerate(params):
+            p.p[i] = float(v)
+        p.prec = self.prec
+        p.flags = 0
+        p.kmax = int(kmax)
+        h = ctypes.c_void_p()
+        _check(lib().tdh_plan_create(self.kind, int(n), ctypes.byref(p), float(tol),
+                                     ctypes.byref(h)))
+        self._h = h
+        K, nn = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().tdh_plan_query(h, ctypes.byref(K), ctypes.byref(nn)))
+        self.K, self.n, self.tol = int(K.value), int(nn.value), float(tol)
+
+    @property
+    def dtype(self):
+        torch = _torch()
+        return torch.float32 if self.prec == FP32 else torch.float64
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tdh_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _run(self, fn, x, out, stream):
+        torch = _torch()
+        host = x.device.type == "cpu"
+        xd = x.to("cuda", non_blocking=True) if host else x
+        if xd.dtype != self.dtype or xd.shape[-1] != self.n or not xd.is_contiguous():
+            raise ValueError(f"expected a contiguous {self.dtype} tensor [..., {self.n}]")
+        batch = xd.numel() // self.n
+        od = out if (out is not None and not host) else torch.empty_like(xd)
+        _check(fn(self._h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(od.data_ptr()),
+                  batch, _stream(stream)))
+        if host:
+            res = out if out is not None else torch.empty(xd.shape, dtype=xd.dtype, pin_memory=True)
+            res.copy_(od, non_blocking=True)
+            return res
+        return od
+
+    def execute(self, x, out=None, stream=None):
+        """beta = A alpha for every vector of x ([..., n], the plan's dtype).  A CUDA tensor
+        runs on `stream` (default: torch's current stream) and returns asynchronously; a CPU
+        tensor is copied in, converted and copied back (synchronise before reading)."""
+        return self._run(lib().tdh_plan_execute, x, out, stream)
+
+    def adjoint(self, g, out=None, stream=None):
+        """A^T g for every vector of g (the transpose product)."""
+        return self._run(lib().tdh_plan_execute_adjoint, g, out, stream)
+
+
+def symbols(kind, n, params=(), stream=None):
+    """Step a1 alone: (t, h, d1, d2) float64 CUDA tensors of the split A = D1 (T o H) D2."""
+    torch = _torch()
+    t = torch.empty(n, dtype=torch.float64, device="cuda")
+    h = torch.empty(2 * n - 1, dtype=torch.float64, device="cuda")
+    d1 = torch.empty(n, dtype=torch.float64, device="cuda")
+    d2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    p = (ctypes.c_double * 4)(*([float(v) for v in params] + [0.0] * (4 - len(params))))
+    ptr = lambda a: ctypes.c_void_p(a.data_ptr())
+    _check(lib().tdh_symbols(_kind(kind), int(n), p, ptr(t), ptr(h), ptr(d1), ptr(d2),
+                             _stream(stream)))
+    return t, h, d1, d2
+
+
+def pchol(h, n, j0, tol, kmax=128, stream=None):
+    """Step a2 alone on a float64 CUDA Hankel generator h[2n-1]: returns (u [K][n], pivots)."""
+    torch = _torch()
+    kmax = int(min(kmax, n - j0))
+    u = torch.zeros((kmax, n), dtype=torch.float64, device="cuda")
+    piv = torch.zeros(kmax, dtype=torch.int64, device="cuda")
+    K = ctypes.c_int64()
+    _check(lib().tdh_pchol(ctypes.c_void_p(h.data_ptr()), int(n), int(j0), float(tol), kmax,
+                           ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(piv.data_ptr()),
+                           ctypes.byref(K), _stream(stream)))
+    return u[: K.value].clone(), piv[: K.value].clone()

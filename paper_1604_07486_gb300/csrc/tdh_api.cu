@@ -1,0 +1,256 @@
+// C ABI: plan construction (Fig. 1 steps 1-2), execution (steps 3-5), queries, errors.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "tdh_internal.cuh"
+
+namespace tdh {
+
+namespace {
+thread_local char g_err[1024];
+}
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+int dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TDH_ERR_NOMEM : TDH_ERR_CUDA;
+    }
+    return TDH_OK;
+}
+
+void dev_free(void* p) {
+    if (p) cudaFree(p);
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+namespace {
+
+void release_step(Step& st) {
+    dev_free(st.t);
+    dev_free(st.h);
+    dev_free(st.d1);
+    dev_free(st.d2);
+    dev_free(st.u64);
+    dev_free(st.piv);
+    dev_free(st.d1x);
+    dev_free(st.d2x);
+    dev_free(st.row0);
+    exec_release(st.ex);
+    st = Step{};
+}
+
+// Build one conversion step: symbols (a1), pivoted Cholesky (a2), execute tables (a3).
+int build_step(Step& st, double tol, int64_t kmax, int prec, cudaStream_t s) {
+    const int64_t n = st.n;
+    TDH_TRY(dev_alloc_t(&st.t, n));
+    TDH_TRY(dev_alloc_t(&st.h, 2 * n - 1));
+    TDH_TRY(dev_alloc_t(&st.d1, n));
+    TDH_TRY(dev_alloc_t(&st.d2, n));
+    TDH_TRY(symbols_launch(st.kind, n, st.p, st.t, st.h, st.d1, st.d2, s));
+    st.j0 = (st.kind == TDH_CHEB2LEG) ? 1 : 0;
+    st.K = 0;
+    if (st.j0 < n) {
+        int64_t kcap = std::min<int64_t>(kmax, n - st.j0);
+        double* ubig = nullptr;
+        TDH_TRY(dev_alloc_t(&st.piv, (size_t)kcap));
+        TDH_TRY(dev_alloc_t(&ubig, (size_t)kcap * n));
+        int64_t K = 0;
+        int rc = pchol_run(st.h, n, st.j0, tol, kcap, ubig, st.piv, &K, s);
+        if (rc == TDH_OK && K > 0) {
+            rc = dev_alloc_t(&st.u64, (size_t)K * n);
+            if (rc == TDH_OK) {
+                cudaError_t e = cudaMemcpyAsync(st.u64, ubig, sizeof(double) * K * n,
+                                                cudaMemcpyDeviceToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) {
+                    set_error("factor copy: %s", cudaGetErrorString(e));
+                    rc = TDH_ERR_CUDA;
+                }
+            }
+        }
+        dev_free(ubig);
+        TDH_TRY(rc);
+        st.K = K;
+    }
+    return exec_prepare(st, prec, s);
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+    auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + bytes && y < x + bytes;
+}
+
+int run(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream, int adjoint) {
+    clear_error();
+    if (!plan) {
+        set_error("NULL plan");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch < 0) {
+        set_error("batch must be >= 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return TDH_OK;
+    if (!in || !out) {
+        set_error("NULL in/out");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (!aligned16(in) || !aligned16(out)) {
+        set_error("in/out must be 16-byte aligned");
+        return TDH_ERR_ALIGN;
+    }
+    const size_t esz = plan->params.prec == TDH_FP32 ? 4 : 8;
+    const size_t bytes = (size_t)batch * (size_t)plan->n_max * esz;
+    if (overlaps(in, out, bytes)) {
+        set_error("out overlaps in");
+        return TDH_ERR_ALIAS;
+    }
+    cudaStream_t s = as_stream(stream);
+    if (plan->steps.size() != 1) {
+        set_error("multi-step plans are not built in this version");
+        return TDH_ERR_UNSUPPORTED;
+    }
+    return exec_launch(plan->steps[0], plan->params.prec, in, out, batch, adjoint, s);
+}
+
+}  // namespace
+}  // namespace tdh
+
+using namespace tdh;
+
+extern "C" {
+
+const char* tdh_last_error(void) { return g_err; }
+
+int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double tol,
+                    tdh_plan_t* out) {
+    clear_error();
+    if (!out || !params) {
+        set_error("NULL params/out");
+        return TDH_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (kind < TDH_LEG2CHEB || kind > TDH_JAC2JAC) {
+        set_error("unknown kind %d", kind);
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (n_max < 1 || !(tol > 0.0) || !std::isfinite(tol)) {
+        set_error("need n_max >= 1 and finite tol > 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (params->prec != TDH_FP32 && params->prec != TDH_FP64) {
+        set_error("unknown precision %d", params->prec);
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (params->kmax < 0) {
+        set_error("kmax must be >= 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (kind == TDH_JAC2JAC) {
+        set_error("Jacobi conversion is not built in this version");
+        return TDH_ERR_UNSUPPORTED;
+    }
+    if (kind == TDH_ULTRA2ULTRA) {
+        double l1 = params->p[0], l2 = params->p[1];
+        if (!(l1 > 0.0) || !(l2 > 0.0)) {
+            set_error("ultraspherical parameters must be > 0");
+            return TDH_ERR_INVALID_ARG;
+        }
+        double d = l1 - l2;
+        if (!(std::fabs(d) < 1.0) || d == 0.0) {
+            set_error("ultraspherical conversion is built for 0 < |l1 - l2| < 1 only");
+            return TDH_ERR_UNSUPPORTED;
+        }
+    }
+    tdh_plan_s* plan = new (std::nothrow) tdh_plan_s;
+    if (!plan) {
+        set_error("host allocation failed");
+        return TDH_ERR_NOMEM;
+    }
+    plan->kind = kind;
+    plan->n_max = n_max;
+    plan->params = *params;
+    plan->tol = tol;
+    cudaGetDevice(&plan->device);
+    const int64_t kmax = params->kmax > 0 ? params->kmax : 128;
+    cudaStream_t s = nullptr;
+    int rc = TDH_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
+        delete plan;
+        return TDH_ERR_CUDA;
+    }
+    Step st;
+    st.kind = kind;
+    st.n = n_max;
+    std::memcpy(st.p, params->p, sizeof(st.p));
+    plan->steps.push_back(st);
+    rc = build_step(plan->steps.back(), tol, kmax, params->prec, s);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc != TDH_OK) {
+        for (auto& x : plan->steps) release_step(x);
+        delete plan;
+        return rc;
+    }
+    *out = plan;
+    return TDH_OK;
+}
+
+int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream) {
+    return run(plan, in, out, batch, stream, 0);
+}
+
+int tdh_plan_execute_adjoint(tdh_plan_t plan, const void* in, void* out, int64_t batch,
+                             void* stream) {
+    return run(plan, in, out, batch, stream, 1);
+}
+
+int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max) {
+    clear_error();
+    if (!plan) {
+        set_error("NULL plan");
+        return TDH_ERR_INVALID_ARG;
+    }
+    int64_t kk = 0;
+    for (const auto& st : plan->steps) kk = std::max(kk, st.K);
+    if (K) *K = kk;
+    if (n_max) *n_max = plan->n_max;
+    return TDH_OK;
+}
+
+int tdh_plan_destroy(tdh_plan_t plan) {
+    clear_error();
+    if (!plan) return TDH_OK;
+    for (auto& st : plan->steps) release_step(st);
+    delete plan;
+    return TDH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,366 @@
+// Host side of the execute path: per-plan tables (step a3 and the kernel's twiddles and
+// factor layout) and the launch dispatch over the kernel instantiations.
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "tdh_exec.cuh"
+
+namespace tdh {
+namespace {
+
+// FFT geometry for a transform of 2^logL points in precision `prec`.
+bool choose_geometry(int prec, int logL, Geometry* g) {
+    g->prec = prec;
+    g->logL = logL;
+    const int cap = (prec == TDH_FP32) ? 14 : 13;  // largest local FFT held in shared memory
+    if (logL <= cap) {
+        g->logLC = logL;
+        g->C = 1;
+    } else {
+        g->logLC = cap;
+        g->C = 1 << (logL - cap);
+    }
+    if (g->C > 8) return false;
+    if (prec == TDH_FP32)
+        g->R = (g->logLC <= 9) ? 8 : 16;
+    else
+        g->R = 8;
+    g->NT = std::min(512, (1 << g->logLC) / g->R);
+    return true;
+}
+
+// Natural frequency of local position pos after the DIF passes (digit reversal).
+int local_freq(const PassGeom& G, int pos) {
+    int rem = pos, f = 0, mult = 1;
+    for (int i = 0; i < G.np(); ++i) {
+        const int s = G.S(i);
+        const int p = rem / s;
+        rem %= s;
+        f += p * mult;
+        mult *= G.rad(i);
+    }
+    return f;
+}
+
+constexpr int kThreads = 256;
+inline unsigned blocks_for(int64_t count) { return (unsigned)((count + kThreads - 1) / kThreads); }
+
+__device__ __forceinline__ double2 omega(int64_t e, int64_t den) {
+    // exp(-2 pi i e / den), argument reduced exactly before sincospi
+    const int64_t r = ((e % den) + den) % den;
+    double s, c;
+    sincospi(2.0 * (double)r / (double)den, &s, &c);
+    return make_double2(c, -s);
+}
+
+template <typename V>
+__device__ __forceinline__ V from_d2(double2 z);
+template <>
+__device__ __forceinline__ float2 from_d2<float2>(double2 z) {
+    return make_float2((float)z.x, (float)z.y);
+}
+template <>
+__device__ __forceinline__ double2 from_d2<double2>(double2 z) {
+    return z;
+}
+
+// symbol of the packed correlation: s_i = t_{2i} for i < m, zero-padded to L
+__global__ void k_fill_symbol(const double* __restrict__ t, int64_t m, int64_t L,
+                              double2* __restrict__ x) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < L) x[i] = make_double2(i < m ? t[2 * i] : 0.0, 0.0);
+}
+
+// one radix-2 Stockham stage (natural order in and out), float64
+__global__ void k_stockham(const double2* __restrict__ x, double2* __restrict__ y, int64_t L,
+                           int64_t m) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= L / 2) return;
+    const int64_t j = i / m, k = i % m;
+    const double2 w = omega(k, 2 * m);
+    const double2 a = x[j * m + k];
+    const double2 b0 = x[j * m + k + L / 2];
+    const double2 b = make_double2(w.x * b0.x - w.y * b0.y, w.x * b0.y + w.y * b0.x);
+    y[2 * j * m + k] = make_double2(a.x + b.x, a.y + b.y);
+    y[2 * j * m + k + m] = make_double2(a.x - b.x, a.y - b.y);
+}
+
+// spec[pos][f2] = conj(S[f1(pos) + LC f2]) / L
+template <typename V>
+__global__ void k_spec(const double2* __restrict__ S, const int* __restrict__ perm, int LC, int C,
+                       int64_t L, V* __restrict__ spec) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= (int64_t)LC * C) return;
+    const int pos = (int)(i / C), f2 = (int)(i % C);
+    const double2 z = S[perm[pos] + (int64_t)LC * f2];
+    const double inv = 1.0 / (double)L;
+    spec[i] = from_d2<V>(make_double2(z.x * inv, -z.y * inv));
+}
+
+// twx[pos] = omega_L^{f1(pos)}
+template <typename V>
+__global__ void k_twx(const int* __restrict__ perm, int LC, int64_t L, V* __restrict__ twx) {
+    int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i < LC) twx[i] = from_d2<V>(omega(perm[i], L));
+}
+
+// out[i] = omega_den^{(i / S) * (i % S)} for i < count (S = count: plain omega_den^i)
+template <typename V>
+__global__ void k_omega_table(V* __restrict__ out, int64_t count, int64_t S, int64_t den) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < count) out[i] = from_d2<V>(omega((i / S) * (i % S), den));
+}
+
+template <typename V>
+__global__ void k_omega_lin(V* __restrict__ out, int64_t count, int64_t den) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < count) out[i] = from_d2<V>(omega(i, den));
+}
+
+// u_dec[r][k1][k2] = (u[r][2a], u[r][2a+1]), a = k1 + C k2 (zero beyond n)
+template <typename T>
+__global__ void k_u_gather(const double* __restrict__ u, int64_t n, int64_t K, int C, int half,
+                           typename cx<T>::t* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t total = K * C * (int64_t)half;
+    if (i >= total) return;
+    const int64_t k2 = i % half;
+    const int64_t k1 = (i / half) % C;
+    const int64_t r = i / ((int64_t)half * C);
+    const int64_t a = k1 + (int64_t)C * k2;
+    const int64_t i0 = 2 * a;
+    const double* ur = u + r * n;
+    T x0 = (i0 < n) ? (T)ur[i0] : T(0);
+    T x1 = (i0 + 1 < n) ? (T)ur[i0 + 1] : T(0);
+    typename cx<T>::t v;
+    v.x = x0;
+    v.y = x1;
+    out[i] = v;
+}
+
+template <typename T>
+__global__ void k_cast(const double* __restrict__ in, T* __restrict__ out, int64_t count) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < count) out[i] = (T)in[i];
+}
+
+// row 0 of A = D1 (T o H) D2 (valid for k >= 1), with A_00 = 1 (Sec. 5.1)
+template <typename T>
+__global__ void k_row0(const double* __restrict__ t, const double* __restrict__ h,
+                       const double* __restrict__ d1, const double* __restrict__ d2, int64_t n,
+                       T* __restrict__ out) {
+    int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (k >= n) return;
+    out[k] = (k == 0) ? T(1) : (T)(d1[0] * t[k] * h[k] * d2[k]);
+}
+
+template <typename T>
+int prepare_typed(Step& st, const Geometry& g, cudaStream_t s) {
+    using V = typename cx<T>::t;
+    ExecData& ex = st.ex;
+    const PassGeom G{g.logLC, g.R};
+    const int LC = G.LC(), C = g.C;
+    const int64_t L = (int64_t)1 << g.logL;
+    const int64_t m = ex.m;
+    int rc = TDH_OK;
+    double2 *x = nullptr, *y = nullptr;
+    int* perm_d = nullptr;
+    std::vector<int> perm(LC);
+    for (int pos = 0; pos < LC; ++pos) perm[pos] = local_freq(G, pos);
+
+    if ((rc = dev_alloc_t(&x, L)) || (rc = dev_alloc_t(&y, L)) || (rc = dev_alloc_t(&perm_d, LC)))
+        goto out;
+    if ((rc = dev_alloc(&ex.spec, sizeof(V) * (size_t)LC * C)) ||
+        (rc = dev_alloc(&ex.tw0, sizeof(V) * (size_t)(LC / g.R))) ||
+        (rc = dev_alloc(&ex.u, sizeof(V) * (size_t)std::max<int64_t>(st.K, 1) * C * (LC / 2))))
+        goto out;
+    ex.twp_len = G.twp_len();
+    if (ex.twp_len > 0 && (rc = dev_alloc(&ex.twp, sizeof(V) * (size_t)ex.twp_len))) goto out;
+    if (C > 1 && (rc = dev_alloc(&ex.twx, sizeof(V) * (size_t)LC))) goto out;
+    {
+        cudaError_t e = cudaMemcpyAsync(perm_d, perm.data(), sizeof(int) * LC,
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            set_error("table upload: %s", cudaGetErrorString(e));
+            rc = TDH_ERR_CUDA;
+            goto out;
+        }
+        // a3: S = DFT_L(s) in float64, natural order, by log2 L Stockham stages
+        k_fill_symbol<<<blocks_for(L), kThreads, 0, s>>>(st.t, m, L, x);
+        for (int64_t mm = 1; mm < L; mm *= 2) {
+            k_stockham<<<blocks_for(L / 2), kThreads, 0, s>>>(x, y, L, mm);
+            std::swap(x, y);
+        }
+        k_spec<V><<<blocks_for((int64_t)LC * C), kThreads, 0, s>>>(x, perm_d, LC, C, L,
+                                                                   (V*)ex.spec);
+        if (C > 1) k_twx<V><<<blocks_for(LC), kThreads, 0, s>>>(perm_d, LC, L, (V*)ex.twx);
+        k_omega_lin<V><<<blocks_for(LC / g.R), kThreads, 0, s>>>((V*)ex.tw0, LC / g.R, LC);
+        for (int i = 1; i <= G.np() - 2; ++i)
+            k_omega_table<V><<<blocks_for(G.M(i)), kThreads, 0, s>>>(
+                (V*)ex.twp + G.twoff(i), G.M(i), G.S(i), G.M(i));
+        if (st.K > 0)
+            k_u_gather<T><<<blocks_for(st.K * C * (int64_t)(LC / 2)), kThreads, 0, s>>>(
+                st.u64, st.n, st.K, C, LC / 2, (V*)ex.u);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("execute tables: %s", cudaGetErrorString(e));
+            rc = TDH_ERR_CUDA;
+        }
+    }
+out:
+    if (x || y || perm_d) cudaStreamSynchronize(s);
+    dev_free(x);
+    dev_free(y);
+    dev_free(perm_d);
+    return rc;
+}
+
+template <typename T>
+int prepare_diagonals(Step& st, cudaStream_t s) {
+    const int64_t n = st.n;
+    TDH_TRY(dev_alloc(&st.d1x, sizeof(T) * n));
+    TDH_TRY(dev_alloc(&st.d2x, sizeof(T) * n));
+    k_cast<T><<<blocks_for(n), kThreads, 0, s>>>(st.d1, (T*)st.d1x, n);
+    k_cast<T><<<blocks_for(n), kThreads, 0, s>>>(st.d2, (T*)st.d2x, n);
+    if (st.kind == TDH_CHEB2LEG) {
+        TDH_TRY(dev_alloc(&st.row0, sizeof(T) * n));
+        k_row0<T><<<blocks_for(n), kThreads, 0, s>>>(st.t, st.h, st.d1, st.d2, n, (T*)st.row0);
+    }
+    TDH_CUDA(cudaGetLastError());
+    return TDH_OK;
+}
+
+// ----------------------------------------------------------------------------- launch
+
+template <typename T, int LOGLC, int R, int C, int NT>
+int launch_inst(const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
+    using V = typename cx<T>::t;
+    constexpr PassGeom G{LOGLC, R};
+    constexpr size_t smem = (size_t)(G.LC() + G.LC() / 2 + G.twp_len()) * sizeof(V);
+    static_assert(smem <= 232448, "shared memory budget");
+    auto kern = exec_kernel<T, LOGLC, R, C, NT>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) {
+        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(attr_err));
+        return TDH_ERR_CUDA;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(batch * C), 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (C > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    TDH_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
+    return TDH_OK;
+}
+
+template <typename T>
+int dispatch(const Geometry& g, const ExecParams<T>& P, int64_t batch, cudaStream_t s);
+
+template <>
+int dispatch<float>(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s) {
+    switch (g.logLC * 16 + g.C) {
+    case 8 * 16 + 1: return launch_inst<float, 8, 8, 1, 32>(P, batch, s);
+    case 9 * 16 + 1: return launch_inst<float, 9, 8, 1, 64>(P, batch, s);
+    case 10 * 16 + 1: return launch_inst<float, 10, 16, 1, 64>(P, batch, s);
+    case 11 * 16 + 1: return launch_inst<float, 11, 16, 1, 128>(P, batch, s);
+    case 12 * 16 + 1: return launch_inst<float, 12, 16, 1, 256>(P, batch, s);
+    case 13 * 16 + 1: return launch_inst<float, 13, 16, 1, 512>(P, batch, s);
+    case 14 * 16 + 1: return launch_inst<float, 14, 16, 1, 512>(P, batch, s);
+    case 14 * 16 + 2: return launch_inst<float, 14, 16, 2, 512>(P, batch, s);
+    case 14 * 16 + 4: return launch_inst<float, 14, 16, 4, 512>(P, batch, s);
+    case 14 * 16 + 8: return launch_inst<float, 14, 16, 8, 512>(P, batch, s);
+    }
+    set_error("no float32 kernel for local length 2^%d, cluster %d", g.logLC, g.C);
+    return TDH_ERR_UNSUPPORTED;
+}
+
+template <>
+int dispatch<double>(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s) {
+    switch (g.logLC * 16 + g.C) {
+    case 8 * 16 + 1: return launch_inst<double, 8, 8, 1, 32>(P, batch, s);
+    case 9 * 16 + 1: return launch_inst<double, 9, 8, 1, 64>(P, batch, s);
+    case 10 * 16 + 1: return launch_inst<double, 10, 8, 1, 128>(P, batch, s);
+    case 11 * 16 + 1: return launch_inst<double, 11, 8, 1, 256>(P, batch, s);
+    case 12 * 16 + 1: return launch_inst<double, 12, 8, 1, 512>(P, batch, s);
+    case 13 * 16 + 1: return launch_inst<double, 13, 8, 1, 512>(P, batch, s);
+    case 13 * 16 + 2: return launch_inst<double, 13, 8, 2, 512>(P, batch, s);
+    case 13 * 16 + 4: return launch_inst<double, 13, 8, 4, 512>(P, batch, s);
+    case 13 * 16 + 8: return launch_inst<double, 13, 8, 8, 512>(P, batch, s);
+    }
+    set_error("no float64 kernel for local length 2^%d, cluster %d", g.logLC, g.C);
+    return TDH_ERR_UNSUPPORTED;
+}
+
+template <typename T>
+int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int adjoint,
+                 cudaStream_t s) {
+    using V = typename cx<T>::t;
+    const ExecData& ex = st.ex;
+    ExecParams<T> P;
+    P.in = static_cast<const T*>(in);
+    P.out = static_cast<T*>(out);
+    P.n = st.n;
+    P.K = st.K;
+    P.u = static_cast<const V*>(ex.u);
+    P.spec = static_cast<const V*>(ex.spec);
+    P.twx = static_cast<const V*>(ex.twx);
+    P.tw0 = static_cast<const V*>(ex.tw0);
+    P.twp = static_cast<const V*>(ex.twp);
+    P.din = static_cast<const T*>(adjoint ? st.d1x : st.d2x);
+    P.dout = static_cast<const T*>(adjoint ? st.d2x : st.d1x);
+    P.row0 = static_cast<const T*>(st.row0);
+    P.adjoint = adjoint;
+    return dispatch<T>(ex.g, P, batch, s);
+}
+
+}  // namespace
+
+int exec_prepare(Step& st, int prec, cudaStream_t s) {
+    ExecData& ex = st.ex;
+    ex.m = (st.n + 1) / 2;
+    int logL = 8;
+    while (((int64_t)1 << logL) < 2 * ex.m - 1) ++logL;
+    if (!choose_geometry(prec, logL, &ex.g)) {
+        set_error("length %lld needs an FFT of 2^%d points, beyond this build's cluster limit",
+                  (long long)st.n, logL);
+        return TDH_ERR_UNSUPPORTED;
+    }
+    if (prec == TDH_FP32) {
+        TDH_TRY(prepare_diagonals<float>(st, s));
+        return prepare_typed<float>(st, ex.g, s);
+    }
+    TDH_TRY(prepare_diagonals<double>(st, s));
+    return prepare_typed<double>(st, ex.g, s);
+}
+
+void exec_release(ExecData& ex) {
+    dev_free(ex.spec);
+    dev_free(ex.twx);
+    dev_free(ex.tw0);
+    dev_free(ex.twp);
+    dev_free(ex.u);
+    ex = ExecData{};
+}
+
+int exec_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
+                cudaStream_t s) {
+    if (prec == TDH_FP32) return launch_typed<float>(st, in, out, batch, adjoint, s);
+    return launch_typed<double>(st, in, out, batch, adjoint, s);
+}
+
+}  // namespace tdh

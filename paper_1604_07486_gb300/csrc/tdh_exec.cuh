@@ -1,0 +1,372 @@
+// Steps a4-a7: the fused execute kernel, beta = D1 sum_r u_r o T (u_r o D2 alpha)
+// (Fig. 1 steps 3-5, eq. (Cdecomposition)), and its adjoint.
+//
+// Layout.  T has the parity structure of the Legendre/Chebyshev/ultraspherical cases
+// (T_jk = 0 for k - j odd), so even and odd indices never mix: with z_a = x_{2a} + i x_{2a+1}
+// both halves are upper-triangular Toeplitz products with the same generator s_m = t_{2m},
+// and one complex correlation y_a = sum_{b>=a} s_{b-a} z_b does both.  The float pairs of a
+// coefficient vector are exactly that complex array, so no shuffle is needed.  Each
+// correlation is a circular one of length L >= 2m - 1 (m = ceil(n/2)): zero-padded FFT,
+// multiply by conj(DFT(s)), inverse FFT (Sec. 1, citing Ng Sec. 3.4).
+//
+// One vector is handled by a cluster of C CTAs (C = 1 when the FFT fits one CTA's shared
+// memory).  CTA k1 of the cluster owns the decimated sequence z[k1 + C k2], k2 < LC = L / C,
+// keeps it and the scaled input in shared memory, and runs all K rank terms:
+//   forward local DIF passes (radix R, natural order in, digit-reversed out)
+//   -> cross-CTA stage through distributed shared memory (twiddle, C-point DFT, symbol
+//      multiply, inverse C-point DFT, conjugate twiddle; fused into one exchange)
+//   -> inverse local DIT passes (digit-reversed in, natural out)
+// accumulating w += u_r o y in registers.  alpha is read once and beta written once.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "tdh_fft.cuh"
+#include "tdh_internal.cuh"
+
+namespace tdh {
+
+namespace cg = cooperative_groups;
+
+// Pass geometry of a local FFT of length 2^LOGLC with radix-R passes and a trailing
+// smaller radix when log2(R) does not divide LOGLC.
+struct PassGeom {
+    int logLC, R;
+    __host__ __device__ constexpr int LC() const { return 1 << logLC; }
+    __host__ __device__ constexpr int logR() const { return ilog2(R); }
+    __host__ __device__ constexpr int npr() const { return logLC / logR(); }
+    __host__ __device__ constexpr int r0() const { return 1 << (logLC - npr() * logR()); }
+    __host__ __device__ constexpr int np() const { return npr() + (r0() > 1 ? 1 : 0); }
+    __host__ __device__ constexpr int rad(int i) const { return i < npr() ? R : r0(); }
+    __host__ __device__ constexpr int M(int i) const {
+        int m = LC();
+        for (int j = 0; j < i; ++j) m /= rad(j);
+        return m;
+    }
+    __host__ __device__ constexpr int S(int i) const { return M(i) / rad(i); }
+    // offset of middle pass i (1 <= i <= np()-2) in the concatenated [p][o] tables
+    __host__ __device__ constexpr int twoff(int i) const {
+        int off = 0;
+        for (int j = 1; j < i; ++j) off += M(j);
+        return off;
+    }
+    __host__ __device__ constexpr int twp_len() const { return twoff(np() - 1); }
+};
+
+template <typename T>
+struct ExecParams {
+    using V = typename cx<T>::t;
+    const T* in;
+    T* out;
+    int64_t n;
+    int64_t K;
+    const V* u;     // [K][C][LC/2]
+    const V* spec;  // [LC][C]
+    const V* twx;   // [LC]
+    const V* tw0;   // [LC/R]
+    const V* twp;   // [twp_len]
+    const T* din;   // D2 (forward) or D1 (adjoint), [n]
+    const T* dout;  // D1 (forward) or D2 (adjoint), [n]
+    const T* row0;  // row 0 applied directly (Chebyshev-to-Legendre), [n], or null
+    int adjoint;
+};
+
+// XOR swizzle of shared-memory element indices: rows of 128 bytes, column ^= row.
+template <typename V>
+__device__ __forceinline__ int swz(int i) {
+    constexpr int epr = 128 / (int)sizeof(V);
+    return i ^ ((i / epr) & (epr - 1));
+}
+
+// powers w^p, p in [0, R), from w^1 by a binary tree of products (error ~ log2(p) ulp)
+template <int R, typename V>
+__device__ __forceinline__ void powers(V w1, V (&wp)[R]) {
+    wp[0] = mk<V>(1, 0);
+    if constexpr (R > 1) wp[1] = w1;
+#pragma unroll
+    for (int p = 2; p < R; ++p) {
+        int hi = 1;
+        while (hi * 2 <= p) hi *= 2;
+        wp[p] = (hi == p) ? cmul(wp[p / 2], wp[p / 2]) : cmul(wp[hi], wp[p - hi]);
+    }
+}
+
+// Middle forward pass i: radix RAD, sub-length M, stride S, twiddles from the [p][o] table.
+template <int RAD, int M, int S, int LC, int NT, typename V>
+__device__ __forceinline__ void pass_fwd(V* buf, const V* tw) {
+#pragma unroll 1
+    for (int g = threadIdx.x; g < LC / RAD; g += NT) {
+        const int b = g / S, o = g % S;
+        const int base = b * M + o;
+        V x[RAD];
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) x[q] = buf[swz<V>(base + q * S)];
+        dif<RAD>(x);
+#pragma unroll
+        for (int jj = 0; jj < RAD; ++jj) {
+            const int p = bitrev(jj, RAD);
+            V y = x[jj];
+            if (p != 0) y = cmul(y, tw[p * S + o]);
+            buf[swz<V>(base + p * S)] = y;
+        }
+    }
+}
+
+template <int RAD, int M, int S, int LC, int NT, typename V>
+__device__ __forceinline__ void pass_inv(V* buf, const V* tw) {
+#pragma unroll 1
+    for (int g = threadIdx.x; g < LC / RAD; g += NT) {
+        const int b = g / S, o = g % S;
+        const int base = b * M + o;
+        V x[RAD];
+#pragma unroll
+        for (int p = 0; p < RAD; ++p) {
+            V y = buf[swz<V>(base + p * S)];
+            if (p != 0) y = cmulc(y, tw[p * S + o]);
+            x[bitrev(p, RAD)] = y;
+        }
+        dit<RAD>(x);
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) buf[swz<V>(base + q * S)] = x[q];
+    }
+}
+
+template <int I, int LOGLC, int R, int NT, typename V>
+__device__ __forceinline__ void middle_fwd(V* buf, const V* twt) {
+    constexpr PassGeom G{LOGLC, R};
+    if constexpr (I <= G.np() - 2) {
+        pass_fwd<G.rad(I), G.M(I), G.S(I), G.LC(), NT>(buf, twt + G.twoff(I));
+        __syncthreads();
+        middle_fwd<I + 1, LOGLC, R, NT>(buf, twt);
+    }
+}
+
+template <int I, int LOGLC, int R, int NT, typename V>
+__device__ __forceinline__ void middle_inv(V* buf, const V* twt) {
+    constexpr PassGeom G{LOGLC, R};
+    if constexpr (I >= 1) {
+        pass_inv<G.rad(I), G.M(I), G.S(I), G.LC(), NT>(buf, twt + G.twoff(I));
+        __syncthreads();
+        middle_inv<I - 1, LOGLC, R, NT>(buf, twt);
+    }
+}
+
+template <typename T, int LOGLC, int R, int C, int NT>
+__global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
+    using V = typename cx<T>::t;
+    constexpr PassGeom G{LOGLC, R};
+    constexpr int LC = G.LC();
+    constexpr int S0 = LC / R;
+    constexpr int J0 = S0 / NT;
+    constexpr int RL = G.rad(G.np() - 1);  // radix of the last pass (stride 1)
+    constexpr int TWP = G.twp_len();
+    static_assert(G.np() >= 2, "local FFT needs at least two passes");
+    static_assert(J0 >= 1 && S0 % NT == 0, "pass-0 groups must divide over threads");
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* buf = reinterpret_cast<V*>(smem_raw);  // [LC], swizzled
+    V* vbuf = buf + LC;                       // [LC/2] scaled input pairs
+    V* twt = vbuf + LC / 2;                   // [TWP] middle-pass twiddles
+    __shared__ T red[NT / 32];
+
+    const int tid = threadIdx.x;
+    int k1 = 0;
+    if constexpr (C > 1) k1 = (int)cg::this_cluster().block_rank();
+    const int64_t vec = blockIdx.x / C;
+    const int64_t n = P.n;
+    const T* in = P.in + vec * n;
+    T* out = P.out + vec * n;
+
+    for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
+    // v = D alpha in packed pairs; row-0 partial sum (Chebyshev-to-Legendre forward)
+    T r0acc = T(0);
+    for (int k2 = tid; k2 < LC / 2; k2 += NT) {
+        const int64_t a = (int64_t)k1 + (int64_t)C * k2;
+        const int64_t i0 = 2 * a;
+        V v = mk<V>(0, 0);
+        if (i0 < n) {
+            const T x0 = in[i0];
+            const T x1 = (i0 + 1 < n) ? in[i0 + 1] : T(0);
+            const T s1 = (i0 + 1 < n) ? P.din[i0 + 1] : T(0);
+            if (P.row0 && !P.adjoint)
+                r0acc += P.row0[i0] * x0 + ((i0 + 1 < n) ? P.row0[i0 + 1] * x1 : T(0));
+            v = mk<V>(x0 * P.din[i0], x1 * s1);
+        }
+        vbuf[k2] = v;
+    }
+    V w0[J0];
+#pragma unroll
+    for (int j = 0; j < J0; ++j) w0[j] = P.tw0[tid + j * NT];
+    V acc[J0][R / 2];
+#pragma unroll
+    for (int j = 0; j < J0; ++j)
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) acc[j][q] = mk<V>(0, 0);
+    __syncthreads();
+
+    V* rbuf[C];
+    if constexpr (C > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+        for (int j = 0; j < C; ++j) rbuf[j] = cl.map_shared_rank(buf, j);
+    } else {
+        rbuf[0] = buf;
+    }
+
+#pragma unroll 1
+    for (int64_t r = 0; r < P.K; ++r) {
+        const V* ur = P.u + ((int64_t)r * C + k1) * (LC / 2);
+        // ---- forward pass 0: inputs u_r o v (upper half zero), radix R, stride S0
+#pragma unroll
+        for (int j = 0; j < J0; ++j) {
+            const int o = tid + j * NT;
+            V x[R];
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) x[q] = cwmul(vbuf[o + q * S0], ur[o + q * S0]);
+            dif_halfzero<R>(x);
+            V wp[R];
+            powers<R>(w0[j], wp);
+#pragma unroll
+            for (int jj = 0; jj < R; ++jj) {
+                const int p = bitrev(jj, R);
+                buf[swz<V>(o + p * S0)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
+            }
+        }
+        __syncthreads();
+        middle_fwd<1, LOGLC, R, NT>(buf, twt);
+        // ---- last pass (stride 1), spectrum, first inverse pass
+        if constexpr (C == 1) {
+#pragma unroll 1
+            for (int g = tid; g < LC / RL; g += NT) {
+                V x[RL];
+#pragma unroll
+                for (int q = 0; q < RL; ++q) x[q] = buf[swz<V>(g * RL + q)];
+                dif<RL>(x);
+#pragma unroll
+                for (int jj = 0; jj < RL; ++jj) {
+                    const V s = P.spec[g * RL + bitrev(jj, RL)];
+                    x[jj] = P.adjoint ? cmulc(x[jj], s) : cmul(x[jj], s);
+                }
+                dit<RL>(x);
+#pragma unroll
+                for (int q = 0; q < RL; ++q) buf[swz<V>(g * RL + q)] = x[q];
+            }
+            __syncthreads();
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+#pragma unroll 1
+            for (int g = tid; g < LC / RL; g += NT) {
+                V x[RL];
+#pragma unroll
+                for (int q = 0; q < RL; ++q) x[q] = buf[swz<V>(g * RL + q)];
+                dif<RL>(x);
+#pragma unroll
+                for (int jj = 0; jj < RL; ++jj) buf[swz<V>(g * RL + bitrev(jj, RL))] = x[jj];
+            }
+            cl.sync();
+            // cross-CTA stage for positions owned by this CTA
+#pragma unroll 1
+            for (int pos = k1 * (LC / C) + tid; pos < (k1 + 1) * (LC / C); pos += NT) {
+                const int sp = swz<V>(pos);
+                const V tw = P.twx[pos];
+                V a[C], twj[C];
+                twj[0] = mk<V>(1, 0);
+#pragma unroll
+                for (int j = 1; j < C; ++j) twj[j] = cmul(twj[j - 1], tw);
+#pragma unroll
+                for (int j = 0; j < C; ++j) a[j] = cmul(rbuf[j][sp], twj[j]);
+                dif<C>(a);
+#pragma unroll
+                for (int jj = 0; jj < C; ++jj) {
+                    const V s = P.spec[(int64_t)pos * C + bitrev(jj, C)];
+                    a[jj] = P.adjoint ? cmulc(a[jj], s) : cmul(a[jj], s);
+                }
+                dit<C>(a);
+#pragma unroll
+                for (int j = 0; j < C; ++j) rbuf[j][sp] = cmulc(a[j], twj[j]);
+            }
+            cl.sync();
+#pragma unroll 1
+            for (int g = tid; g < LC / RL; g += NT) {
+                V x[RL];
+#pragma unroll
+                for (int p = 0; p < RL; ++p) x[bitrev(p, RL)] = buf[swz<V>(g * RL + p)];
+                dit<RL>(x);
+#pragma unroll
+                for (int q = 0; q < RL; ++q) buf[swz<V>(g * RL + q)] = x[q];
+            }
+            __syncthreads();
+        }
+        middle_inv<G.np() - 2, LOGLC, R, NT>(buf, twt);
+        // ---- inverse pass 0: outputs [0, LC/2) only, accumulate u_r o y
+#pragma unroll
+        for (int j = 0; j < J0; ++j) {
+            const int o = tid + j * NT;
+            V wp[R];
+            powers<R>(w0[j], wp);
+            V x[R];
+#pragma unroll
+            for (int p = 0; p < R; ++p) {
+                const V y = buf[swz<V>(o + p * S0)];
+                x[bitrev(p, R)] = (p == 0) ? y : cmulc(y, wp[p]);
+            }
+            dit_halfout<R>(x);
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) {
+                const V uu = ur[o + q * S0];
+                acc[j][q].x = fma(uu.x, x[q].x, acc[j][q].x);
+                acc[j][q].y = fma(uu.y, x[q].y, acc[j][q].y);
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- epilogue: beta = D1 w (forward) / D2 w (adjoint), row 0, write once
+    T g0 = T(0);
+    if (P.row0 && P.adjoint) g0 = in[0];
+#pragma unroll
+    for (int j = 0; j < J0; ++j) {
+        const int o = tid + j * NT;
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) {
+            const int64_t a = (int64_t)k1 + (int64_t)C * (o + q * S0);
+            const int64_t i0 = 2 * a;
+            if (i0 < n) {
+                T b0 = acc[j][q].x * P.dout[i0];
+                if (P.row0 && P.adjoint) b0 += P.row0[i0] * g0;
+                out[i0] = b0;
+                if (i0 + 1 < n) {
+                    T b1 = acc[j][q].y * P.dout[i0 + 1];
+                    if (P.row0 && P.adjoint) b1 += P.row0[i0 + 1] * g0;
+                    out[i0 + 1] = b1;
+                }
+            }
+        }
+    }
+    if (P.row0 && !P.adjoint) {
+        // beta_0 = sum_k A_0k alpha_k: block reduction, then across the cluster
+        for (int off = 16; off > 0; off >>= 1) r0acc += __shfl_down_sync(0xffffffffu, r0acc, off);
+        if ((tid & 31) == 0) red[tid >> 5] = r0acc;
+        __syncthreads();
+        if (tid == 0) {
+            T s = T(0);
+            for (int w = 0; w < NT / 32; ++w) s += red[w];
+            red[0] = s;
+        }
+        if constexpr (C > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            if (k1 == 0 && tid == 0) {
+                T s = T(0);
+                for (int j = 0; j < C; ++j) s += *cl.map_shared_rank(&red[0], j);
+                out[0] = s;
+            }
+            cl.sync();
+        } else {
+            __syncthreads();
+            if (tid == 0) out[0] = red[0];
+        }
+    }
+}
+
+}  // namespace tdh

@@ -1,0 +1,115 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "tdh.h"
+
+namespace tdh {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define TDH_CUDA(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::tdh::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),     \
+                             __FILE__, __LINE__);                                        \
+            return TDH_ERR_CUDA;                                                         \
+        }                                                                                \
+    } while (0)
+
+#define TDH_TRY(expr)                                                                    \
+    do {                                                                                 \
+        int rc_ = (expr);                                                                \
+        if (rc_ != TDH_OK) return rc_;                                                   \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Device allocation that records failures as TDH_ERR_NOMEM.
+int dev_alloc(void** p, size_t bytes);
+template <typename T>
+int dev_alloc_t(T** p, size_t count) {
+    return dev_alloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+void dev_free(void* p);
+
+int sm_count();
+
+// ----------------------------------------------------------------------------- a1
+// Fill t[n], h[2n-1], d1[n], d2[n] (device, float64) for `kind`; p = kind parameters.
+int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, double* d1,
+                   double* d2, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- a2
+// Pivoted Cholesky of H[j,k] = h[j+k], j,k in [j0,n); u: [kmax][n]; pivots: [kmax].
+// *K receives the rank (synchronises `s`).
+int pchol_run(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, double* u,
+              int64_t* pivots, int64_t* K, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- a3-a7
+// FFT geometry of one execute configuration: L = C * LC points, local radix R.
+struct Geometry {
+    int prec;   // TDH_FP32 / TDH_FP64
+    int logL;   // L = 2^logL complex points
+    int logLC;  // per-CTA local length
+    int C;      // cluster size (CTAs per vector)
+    int R;      // radix of the local passes
+    int NT;     // threads per CTA
+};
+
+// Device data of one execute configuration.
+struct ExecData {
+    Geometry g{};
+    int64_t m = 0;        // complex length of the packed vector (ceil(n/2))
+    void* spec = nullptr; // [LC][C] complex: conj(DFT(symbol)) / L in the kernel's order
+    void* twx = nullptr;  // [LC] complex: omega_L^{f1(pos)} (C > 1)
+    void* tw0 = nullptr;  // [LC/R] complex: omega_LC^o, pass-0 twiddle bases
+    void* twp = nullptr;  // later-pass twiddle tables, concatenated [p][o] blocks
+    int64_t twp_len = 0;  // complex entries in twp
+    void* u = nullptr;    // [K][C][LC/2] complex: factors decimated by C (packed pairs)
+};
+
+// One T o H conversion step of a plan.
+struct Step {
+    int kind = 0;
+    double p[4] = {0, 0, 0, 0};
+    int64_t n = 0;
+    int64_t K = 0;
+    int64_t j0 = 0;
+    double* t = nullptr;   // [n]
+    double* h = nullptr;   // [2n-1]
+    double* d1 = nullptr;  // [n]
+    double* d2 = nullptr;  // [n]
+    double* u64 = nullptr; // [K][n]
+    int64_t* piv = nullptr;
+    void* d1x = nullptr;   // diagonals in execute precision
+    void* d2x = nullptr;
+    void* row0 = nullptr;  // CHEB2LEG: row 0 of A in execute precision, else null
+    ExecData ex;
+};
+
+}  // namespace tdh
+
+struct tdh_plan_s {
+    int kind = 0;
+    int64_t n_max = 0;
+    tdh_params params{};
+    double tol = 0;
+    int device = 0;
+    std::vector<tdh::Step> steps;
+};
+
+namespace tdh {
+// Build the execute configuration of `st` for precision `prec` (spectrum, twiddles, factors).
+int exec_prepare(Step& st, int prec, cudaStream_t s);
+void exec_release(ExecData& ex);
+// beta = A alpha (adjoint = 0) or A^T g (adjoint = 1) for one step.
+int exec_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
+                cudaStream_t s);
+}  // namespace tdh

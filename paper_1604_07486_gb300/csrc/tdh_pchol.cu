@@ -1,0 +1,217 @@
+// Step a2: pivoted Cholesky of a positive semidefinite Hankel block, O(K^2 N), in float64
+// (Sec. 2.1, Fig. 2).
+//
+// Only the diagonal d and the K selected columns are ever formed.  Step r:
+//   p_r = argmax_j d_j                      (lowest index on ties)
+//   c   = H[:, p_r] - sum_{i<r} u_i u_i[p_r]   (earlier steps applied to column p_r)
+//   a_r = c[p_r];  u_r = c / sqrt(a_r);  d <- d - u_r^2
+// and the factorisation stops before any step whose pivot (max d, or a_r) is
+// <= tol * max(diag H).  u_r = l_r / sqrt(a_r) in the paper's notation, so
+// H ~ sum_r l_r l_r^T / a_r = sum_r u_r u_r^T.
+//
+// One launch per step over a grid of blocks; each block owns a fixed slice of indices and
+// also publishes the argmax of its slice of the updated d, which every block of the next
+// step reduces (a few hundred entries) to find the next pivot.  Every block takes the same
+// stop decision from the same data, so no grid-wide wait is needed.  The host reads the
+// "done" flag every few steps and stops launching.
+#include <cmath>
+
+#include "tdh_internal.cuh"
+
+namespace tdh {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kKmaxShared = 1024;  // u_i[p] for i < r staged in shared memory
+
+struct ArgMax {
+    double v;
+    int64_t i;
+};
+
+struct State {
+    double thresh;  // tol * d0
+    int64_t K;      // steps taken so far
+    int done;
+};
+
+__device__ __forceinline__ ArgMax amax(ArgMax a, ArgMax b) {
+    return (b.v > a.v || (b.v == a.v && b.i < a.i)) ? b : a;
+}
+
+__device__ ArgMax block_argmax(ArgMax x) {
+    __shared__ double sv[kThreads / 32];
+    __shared__ int64_t si[kThreads / 32];
+    for (int off = 16; off > 0; off >>= 1) {
+        ArgMax o;
+        o.v = __shfl_down_sync(0xffffffffu, x.v, off);
+        o.i = __shfl_down_sync(0xffffffffu, x.i, off);
+        x = amax(x, o);
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sv[w] = x.v;
+        si[w] = x.i;
+    }
+    __syncthreads();
+    if (w == 0) {
+        x.v = (l < kThreads / 32) ? sv[l] : -INFINITY;
+        x.i = (l < kThreads / 32) ? si[l] : INT64_MAX;
+        for (int off = 16; off > 0; off >>= 1) {
+            ArgMax o;
+            o.v = __shfl_down_sync(0xffffffffu, x.v, off);
+            o.i = __shfl_down_sync(0xffffffffu, x.i, off);
+            x = amax(x, o);
+        }
+        if (l == 0) {
+            sv[0] = x.v;
+            si[0] = x.i;
+        }
+    }
+    __syncthreads();
+    ArgMax r{sv[0], si[0]};
+    __syncthreads();
+    return r;
+}
+
+// d_j = H_jj = h[2j] for j >= j0 (excluded indices get -inf); publish block argmax.
+__global__ void __launch_bounds__(kThreads) pchol_init(const double* __restrict__ h, int64_t n,
+                                                       int64_t j0, double* __restrict__ d,
+                                                       ArgMax* __restrict__ part) {
+    ArgMax best{-INFINITY, INT64_MAX};
+    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * kThreads) {
+        double v = (j >= j0) ? h[2 * j] : -INFINITY;
+        d[j] = v;
+        best = amax(best, ArgMax{v, j});
+    }
+    best = block_argmax(best);
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
+}
+
+__global__ void __launch_bounds__(kThreads) pchol_step(
+    const double* __restrict__ h, int64_t n, int64_t j0, double tol, int r,
+    double* __restrict__ u, int64_t* __restrict__ piv, double* __restrict__ d,
+    const ArgMax* __restrict__ part_in, ArgMax* __restrict__ part_out, int nparts,
+    State* __restrict__ st) {
+    __shared__ double s_up[kKmaxShared];
+    __shared__ double s_a;
+    if (st->done) return;
+    // every block reduces the same partials: identical pivot and decision everywhere
+    ArgMax best{-INFINITY, INT64_MAX};
+    for (int i = threadIdx.x; i < nparts; i += kThreads) best = amax(best, part_in[i]);
+    best = block_argmax(best);
+    double thresh = (r == 0) ? tol * best.v : st->thresh;
+    if (r == 0 && blockIdx.x == 0 && threadIdx.x == 0) st->thresh = thresh;
+    const int64_t p = best.i;
+    if (!(best.v > thresh) || p < j0 || p >= n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->K = r;
+            st->done = 1;
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < r; i += kThreads) s_up[i] = u[(int64_t)i * n + p];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = h[2 * p];
+        for (int i = 0; i < r; ++i) a -= s_up[i] * s_up[i];
+        s_a = a;
+    }
+    __syncthreads();
+    const double a = s_a;
+    if (!(a > thresh)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->K = r;
+            st->done = 1;
+        }
+        return;
+    }
+    const double inv = 1.0 / sqrt(a);
+    ArgMax nb{-INFINITY, INT64_MAX};
+    double* ur = u + (int64_t)r * n;
+    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * kThreads) {
+        double val = 0.0;
+        double dj = -INFINITY;
+        if (j >= j0) {
+            double c = h[j + p];
+            for (int i = 0; i < r; ++i) c -= u[(int64_t)i * n + j] * s_up[i];
+            val = c * inv;
+            dj = d[j] - val * val;
+            d[j] = dj;
+        }
+        ur[j] = val;
+        nb = amax(nb, ArgMax{dj, j});
+    }
+    nb = block_argmax(nb);
+    if (threadIdx.x == 0) part_out[blockIdx.x] = nb;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        piv[r] = p;
+        st->K = r + 1;
+    }
+}
+
+}  // namespace
+
+int pchol_run(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, double* u,
+              int64_t* pivots, int64_t* K, cudaStream_t s) {
+    if (kmax > kKmaxShared) kmax = kKmaxShared;
+    if (kmax > n - j0) kmax = n - j0;
+    int nblk = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 4 * (int64_t)sm_count());
+    if (nblk < 1) nblk = 1;
+    double* d = nullptr;
+    ArgMax* part = nullptr;
+    State* st = nullptr;
+    int rc = TDH_OK;
+    State host{0.0, 0, 0};
+    if ((rc = dev_alloc_t(&d, (size_t)n)) != TDH_OK) goto done;
+    if ((rc = dev_alloc_t(&part, (size_t)2 * nblk)) != TDH_OK) goto done;
+    if ((rc = dev_alloc_t(&st, 1)) != TDH_OK) goto done;
+    {
+        cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
+        if (e == cudaSuccess) {
+            pchol_init<<<nblk, kThreads, 0, s>>>(h, n, j0, d, part);
+            e = cudaGetLastError();
+        }
+        for (int64_t r = 0; e == cudaSuccess && r < kmax; ++r) {
+            pchol_step<<<nblk, kThreads, 0, s>>>(h, n, j0, tol, (int)r, u, pivots, d,
+                                                 part + (r & 1) * nblk,
+                                                 part + ((r + 1) & 1) * nblk, nblk, st);
+            e = cudaGetLastError();
+            if (e == cudaSuccess && ((r & 7) == 7 || r + 1 == kmax)) {
+                e = cudaMemcpyAsync(&host, st, sizeof(State), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e == cudaSuccess && host.done) break;
+            }
+        }
+        if (e == cudaSuccess) {
+            e = cudaMemcpyAsync(&host, st, sizeof(State), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        if (e != cudaSuccess) {
+            set_error("pivoted Cholesky: %s", cudaGetErrorString(e));
+            rc = TDH_ERR_CUDA;
+        }
+    }
+    if (rc == TDH_OK) *K = host.K;
+done:
+    if (d || part || st) cudaStreamSynchronize(s);
+    dev_free(d);
+    dev_free(part);
+    dev_free(st);
+    return rc;
+}
+
+}  // namespace tdh
+
+extern "C" int tdh_pchol(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax,
+                         double* u, int64_t* pivots, int64_t* K, void* stream) {
+    tdh::clear_error();
+    if (n < 1 || (j0 != 0 && j0 != 1) || j0 >= n || !(tol > 0.0) || kmax < 1 || !h || !u ||
+        !pivots || !K) {
+        tdh::set_error("tdh_pchol: need n >= 1, j0 in {0,1} < n, tol > 0, kmax >= 1, non-NULL");
+        return TDH_ERR_INVALID_ARG;
+    }
+    return tdh::pchol_run(h, n, j0, tol, kmax, u, pivots, K, tdh::as_stream(stream));
+}

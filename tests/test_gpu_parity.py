@@ -1,0 +1,210 @@
+"""CUDA path against the CPU oracle, element by element (needs a GPU).
+
+Tolerances (max |beta - beta_ref| / ||alpha||_1): float64 1e-12, float32 5e-6.  Inputs are the
+seeded workloads of workloads.py.  Each step of the path is checked on its own through the
+C ABI (symbols a1, pivoted Cholesky a2) and end to end (a3-a7).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 5e-6}
+OKIND = {"leg2cheb": oracle.LEG2CHEB, "cheb2leg": oracle.CHEB2LEG, "ultra2ultra": oracle.ULTRA}
+
+
+@pytest.fixture(scope="module")
+def tdh():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_07486_gb300 as m
+    from paper_1604_07486_gb300 import build
+    build.build()
+    return m
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _rel_err(y, ref, alpha):
+    return (np.abs(y - ref).max(axis=-1) / np.abs(alpha).sum(axis=-1)).max()
+
+
+def _run(tdh, kind, n, batch, prec, tol, decay=1.0, params=(), seed=0):
+    torch = _torch()
+    alpha = workloads.coefficients(n, batch, decay=decay, seed=seed)
+    plan = tdh.Plan(kind, n, prec=prec, tol=tol, params=params)
+    x = torch.tensor(alpha, dtype=plan.dtype, device="cuda")
+    y = plan.execute(x)
+    torch.cuda.synchronize()
+    return plan, alpha, y.double().cpu().numpy()
+
+
+# ------------------------------------------------------------------------------- a1
+
+@pytest.mark.parametrize("kind,params", [("leg2cheb", ()), ("cheb2leg", ()),
+                                         ("ultra2ultra", (0.75, 1.25)),
+                                         ("jac2jac", (0.1, -0.3, 0.0))])
+@pytest.mark.parametrize("n", [37, 4096, 1 << 20])
+def test_symbols(tdh, kind, params, n):
+    """Gamma-ratio symbols on the GPU (asymptotic series) vs the oracle's double-double
+    recurrences: a few ulp relative, including arguments near 2^20 where log-gamma
+    differences would lose five digits."""
+    okind = {"leg2cheb": oracle.LEG2CHEB, "cheb2leg": oracle.CHEB2LEG,
+             "ultra2ultra": oracle.ULTRA, "jac2jac": oracle.JAC}[kind]
+    got = [a.cpu().numpy() for a in tdh.symbols(kind, n, params)]
+    ref = oracle.split(okind, params, n)
+    for name, g, r in zip(("t", "h", "d1", "d2"), got, ref):
+        scale = np.maximum(np.abs(r), 1e-300)
+        rel = (np.abs(g - r) / scale).max()
+        assert rel < 2e-14, (name, rel)
+        assert np.array_equal(g == 0, r == 0), name
+
+
+# ------------------------------------------------------------------------------- a2
+
+@pytest.mark.parametrize("kind,j0", [("leg2cheb", 0), ("cheb2leg", 1)])
+@pytest.mark.parametrize("n,tol", [(301, 1e-15), (5000, 1e-10), (65536, 1e-15)])
+def test_pchol(tdh, kind, j0, n, tol):
+    """GPU pivoted Cholesky on the oracle's Hankel generator vs the oracle's Fig. 2 algorithm:
+    same pivots, same rank (up to the last step near the threshold), same factors."""
+    torch = _torch()
+    okind = OKIND[kind]
+    _, h, _, _ = oracle.split(okind, None, n)
+    u, piv = tdh.pchol(torch.tensor(h, device="cuda"), n, j0, tol)
+    u, piv = u.cpu().numpy(), piv.cpu().numpy()
+    ur, pr = oracle.hankel_factors(okind, None, n, tol)
+    assert abs(len(piv) - len(pr)) <= 1 and min(len(piv), len(pr)) >= 10
+    # steps whose pivot is far above the rounding level are deterministic: same pivot and
+    # same column; later ones may legitimately differ in rounding
+    a = np.array([ur[r, pr[r]] ** 2 for r in range(len(pr))])
+    K = int(np.sum(a > 1e-8 * a[0]))
+    assert np.array_equal(piv[:K], pr[:K])
+    assert np.abs(u[:K] - ur[:K]).max() < 1e-9 * np.abs(ur).max()
+    # the approximation itself on a sampled block
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(np.arange(j0, n), size=min(200, n - j0), replace=False))
+    Hb = h[rows[:, None] + rows[None, :]]
+    approx = u[:, rows].T @ u[:, rows]
+    assert np.abs(Hb - approx).max() <= 4 * tol * h[2 * j0]
+
+
+# ---------------------------------------------------------------------------- a3-a6
+
+@pytest.mark.parametrize("kind", ["leg2cheb", "cheb2leg"])
+@pytest.mark.parametrize("prec,tol", [("fp64", None), ("fp32", None)])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 100, 256, 257, 1000, 1024, 4097, 8192, 16385, 30000])
+def test_execute_small(tdh, kind, prec, tol, n):
+    """Dense oracle on every row, several tiles and ragged tails, both directions."""
+    if tol is None:
+        tol = {("leg2cheb", "fp64"): 1e-15, ("cheb2leg", "fp64"): 1e-17,
+               ("leg2cheb", "fp32"): 1e-7, ("cheb2leg", "fp32"): 1e-10}[(kind, prec)]
+    batch = 3
+    plan, alpha, y = _run(tdh, kind, n, batch, prec, tol, decay=0.5)
+    ref = oracle.matvec(OKIND[kind], None, alpha)
+    err = _rel_err(y, ref, alpha)
+    assert err <= TOL[prec], (err, plan.K)
+
+
+def test_config1_leg2cheb_n1024_fp64(tdh):
+    """Legendre -> Chebyshev, n = 1024, one vector, float64, alpha_k = z_k/(k+1), tol 1e-15."""
+    plan, alpha, y = _run(tdh, "leg2cheb", 1024, 1, "fp64", 1e-15, decay=1.0)
+    ref = oracle.matvec(oracle.LEG2CHEB, None, alpha)
+    assert _rel_err(y, ref, alpha) <= 1e-12
+    assert 20 <= plan.K <= 40
+
+
+@pytest.mark.parametrize("kind,prec,tol", [("leg2cheb", "fp32", 1e-7), ("leg2cheb", "fp64", 1e-15),
+                                           ("cheb2leg", "fp32", 1e-10), ("cheb2leg", "fp64", 1e-17)])
+def test_config2_n65536_single_vector_dense(tdh, kind, prec, tol):
+    """n = 2^16, one vector, alpha_k = z_k/(k+1)^0.5: every row against the dense oracle."""
+    plan, alpha, y = _run(tdh, kind, 1 << 16, 1, prec, tol, decay=0.5)
+    ref = oracle.matvec(OKIND[kind], None, alpha)
+    assert _rel_err(y, ref, alpha) <= TOL[prec]
+
+
+@pytest.mark.parametrize("kind,prec,tol", [("leg2cheb", "fp32", 1e-7), ("cheb2leg", "fp32", 1e-10),
+                                           ("leg2cheb", "fp64", 1e-15)])
+def test_config2_n65536_batch256_sampled(tdh, kind, prec, tol):
+    """The bench's launch: batch 256 of n = 2^16.  Sampled rows (first, last, random) of
+    eight vectors spread over the batch against the oracle, row by row."""
+    n, batch = 1 << 16, 256
+    plan, alpha, y = _run(tdh, kind, n, batch, prec, tol, decay=0.5)
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([np.arange(64), n - 1 - np.arange(64),
+                                     rng.integers(0, n, 128)]))
+    vecs = np.array([0, 37, 100, 128, 200, 254, 255, 17])
+    ref = oracle.matvec(OKIND[kind], None, alpha[vecs], rows=rows)
+    err = (np.abs(y[vecs][:, rows] - ref).max(axis=1) / np.abs(alpha[vecs]).sum(axis=1)).max()
+    assert err <= TOL[prec]
+    assert np.all(np.isfinite(y))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-15), ("fp32", 1e-7)])
+def test_ultraspherical_case2(tdh, prec, tol):
+    """C^(3/4) -> C^(5/4) (Sec. 5.2 Case 2) against the dense oracle."""
+    n = 5000
+    plan, alpha, y = _run(tdh, "ultra2ultra", n, 2, prec, tol, decay=1.0, params=(0.75, 1.25))
+    ref = oracle.matvec(oracle.ULTRA, (0.75, 1.25), alpha)
+    assert _rel_err(y, ref, alpha) <= TOL[prec]
+
+
+# ------------------------------------------------------------------------------- a7
+
+@pytest.mark.parametrize("kind", ["leg2cheb", "cheb2leg"])
+@pytest.mark.parametrize("prec,tol", [("fp64", None), ("fp32", None)])
+@pytest.mark.parametrize("n", [5, 1000, 8192, 40000])
+def test_adjoint(tdh, kind, prec, tol, n):
+    """A^T g against the oracle's dense transpose, and <A a, g> = <a, A^T g>."""
+    torch = _torch()
+    if tol is None:
+        tol = {("leg2cheb", "fp64"): 1e-15, ("cheb2leg", "fp64"): 1e-17,
+               ("leg2cheb", "fp32"): 1e-7, ("cheb2leg", "fp32"): 1e-10}[(kind, prec)]
+    plan = tdh.Plan(kind, n, prec=prec, tol=tol)
+    g = workloads.cotangent(n, 2, seed=3)
+    a = workloads.coefficients(n, 2, decay=1.0, seed=4)
+    gt = torch.tensor(g, dtype=plan.dtype, device="cuda")
+    at = torch.tensor(a, dtype=plan.dtype, device="cuda")
+    atg = plan.adjoint(gt).double().cpu().numpy()
+    aa = plan.execute(at).double().cpu().numpy()
+    rows = np.arange(n) if n <= 8192 else np.unique(np.r_[np.arange(100), n - 1 - np.arange(100),
+                                                         np.random.default_rng(2).integers(0, n, 200)])
+    ref = oracle.matvec(OKIND[kind], None, g, rows=rows, transpose=True)
+    err = (np.abs(atg[:, rows] - ref).max(axis=1) / np.abs(g).sum(axis=1)).max()
+    assert err <= TOL[prec], err
+    lhs = (aa * g).sum(axis=1)
+    rhs = (a * atg).sum(axis=1)
+    scale = np.abs(aa).sum(axis=1) * np.abs(g).max(axis=1) + np.abs(a).sum(axis=1) * np.abs(atg).max(axis=1)
+    assert np.all(np.abs(lhs - rhs) <= 10 * TOL[prec] * scale)
+
+
+# ------------------------------------------------------------------------------- errors
+
+def test_error_paths(tdh):
+    torch = _torch()
+    plan = tdh.Plan("leg2cheb", 100, prec="fp32")
+    x = torch.zeros(2, 100, device="cuda")
+    assert tdh.lib().tdh_plan_execute(plan._h, None, None, 1, None) == -1
+    buf = torch.zeros(1000, device="cuda")
+    import ctypes
+    rc = tdh.lib().tdh_plan_execute(plan._h, ctypes.c_void_p(buf.data_ptr() + 4),
+                                    ctypes.c_void_p(buf.data_ptr() + 512), 1, None)
+    assert rc == -4
+    rc = tdh.lib().tdh_plan_execute(plan._h, ctypes.c_void_p(buf.data_ptr()),
+                                    ctypes.c_void_p(buf.data_ptr() + 256), 1, None)
+    assert rc == -7
+    assert tdh.lib().tdh_plan_execute(plan._h, ctypes.c_void_p(buf.data_ptr()),
+                                      ctypes.c_void_p(buf.data_ptr() + 1024), 0, None) == 0
+    with pytest.raises(tdh.TdhError):
+        tdh.Plan("jac2jac", 100, params=(0.1, -0.3, 0.0, 0.0))
+    with pytest.raises(tdh.TdhError):
+        tdh.Plan("ultra2ultra", 100, params=(-1.0, 0.5))
+    y = plan.execute(x)
+    torch.cuda.synchronize()
+    assert torch.all(y == 0)
