@@ -1,0 +1,369 @@
+"""Throughput of the Legendre <-> Chebyshev conversion on one GB300 (or N, one rank each).
+
+One step = beta = A alpha for a batch of 256 vectors of n = 2^16 coefficients in both
+directions (Legendre -> Chebyshev and Chebyshev -> Legendre), float32 execute with plans
+built in float64 beforehand (plans are made once and reused for every product, as the paper
+does; plan time is reported separately).  Inputs alpha_k = z_k / (k+1)^0.5, z ~ N(0,1) from
+seed 0 (synthetic; the paper's Julia vectors are not reproducible).
+
+Prints one JSON line.  value = coefficients converted per second over all ranks, measured
+on the device with CUDA events around each step, L2 flushed (256 MB write) between steps.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1 << 16
+BATCH = 256
+KINDS = ("leg2cheb", "cheb2leg")
+TOL32 = {"leg2cheb": 1e-7, "cheb2leg": 1e-10}
+TOL64 = {"leg2cheb": 1e-15, "cheb2leg": 1e-17}
+DECAY = 0.5
+WORKLOAD = "leg2cheb+cheb2leg n=65536 batch=256"
+METRIC = "Leg<->Cheb coefficients/s"
+PROFILE = os.path.join(ROOT, "profiles", "exec_fp32_n65536_b256.txt")
+KERNEL_SOURCES = ["paper_1604_07486_gb300/csrc/tdh_exec.cuh", "paper_1604_07486_gb300/csrc/tdh_fft.cuh"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def flops_per_vector(K, L):
+    """Algorithmic flops of one vector: per rank term a forward and an inverse complex FFT of
+    L points (5 L log2 L each), the spectrum multiply (6 L), and the scalings on the way in
+    and out (2 and 4 flops per packed point, L/2 points each)."""
+    import math
+    return K * (10 * L * math.log2(L) + 6 * L + 3 * L)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def profile_traffic():
+    """dram bytes per launch from the committed ncu summary, if it matches this kernel."""
+    try:
+        vals = {}
+        with open(PROFILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def oracle_error(alpha, y, kind, vecs, rows):
+    import numpy as np
+    import oracle
+    ok = {"leg2cheb": oracle.LEG2CHEB, "cheb2leg": oracle.CHEB2LEG}[kind]
+    ref = oracle.matvec(ok, None, alpha[vecs], rows=rows)
+    return float((np.abs(y[vecs][:, rows] - ref).max(axis=1) / np.abs(alpha[vecs]).sum(axis=1)).max())
+
+
+def run_reference(args, rank, world):
+    """The oracle (dense double-double Direct product) timed on the host cores."""
+    import numpy as np
+    import oracle
+    import workloads
+    if rank != 0:
+        return
+    rows_per = 2048
+    alpha = workloads.coefficients(N, 1, decay=DECAY, seed=0)
+    rng = np.random.default_rng(7)
+    kinds = {"leg2cheb": oracle.LEG2CHEB, "cheb2leg": oracle.CHEB2LEG}
+
+    def step(i):
+        rows = np.sort(rng.choice(N, rows_per, replace=False))
+        for k in KINDS:
+            oracle.matvec(kinds[k], None, alpha, rows=rows)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    dt = time.perf_counter() - t0
+    coeffs = 2 * rows_per * args.steps
+    value = coeffs / dt
+    cores = oracle.threads()
+    line = {"metric": METRIC, "value": value, "unit": "coeffs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (double-double accumulation)", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": N, "batch_per_gpu": BATCH, "kinds": list(KINDS),
+                       "decay": DECAY},
+            "cpu_baseline": {"value": value, "unit": "coeffs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{rows_per} rows x 2 directions of one n=65536 vector per step"},
+            "e2e": {"value": value, "unit": "coeffs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """Oracle on one full vector (every row, both directions) on the host cores."""
+    import oracle
+    import workloads
+    alpha = workloads.coefficients(N, 1, decay=DECAY, seed=0)
+    t0 = time.perf_counter()
+    oracle.matvec(oracle.LEG2CHEB, None, alpha)
+    oracle.matvec(oracle.CHEB2LEG, None, alpha)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * N / dt, "unit": "coeffs/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "one n=65536 vector, all rows, both directions (dense double-double)",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1604_07486_gb300 as tdh
+    from paper_1604_07486_gb300 import build
+    import workloads
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # plans (float64 construction on the GPU, timed separately)
+    t0 = time.perf_counter()
+    plans32 = {k: tdh.Plan(k, N, prec="fp32", tol=TOL32[k]) for k in KINDS}
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0) / len(KINDS)
+
+    alpha = workloads.coefficients(N, BATCH, decay=DECAY, seed=rank)
+    xs = {k: torch.tensor(alpha, dtype=torch.float32, device="cuda") for k in KINDS}
+    ys = {k: torch.empty_like(xs[k]) for k in KINDS}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(p, x, y):
+        for k in KINDS:
+            p[k].execute(x[k], out=y[k])
+
+    for _ in range(args.warmup):
+        step(plans32, xs, ys)
+    barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    with sampler:
+        barrier()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            plans32["leg2cheb"].execute(xs["leg2cheb"], out=ys["leg2cheb"])
+            ev[i][1].record(stream)
+            plans32["cheb2leg"].execute(xs["cheb2leg"], out=ys["cheb2leg"])
+            ev[i][2].record(stream)
+        barrier()
+        wall = time.perf_counter() - wall0
+    t_l2c = [e[0].elapsed_time(e[1]) for e in ev]
+    t_c2l = [e[1].elapsed_time(e[2]) for e in ev]
+    step_ms = [a + b for a, b in zip(t_l2c, t_c2l)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    coeffs_per_step = len(KINDS) * BATCH * N
+    value = world * coeffs_per_step * args.steps / (total_ms / 1e3)
+
+    # roofline of the execute kernel (the only kernel in the timed region)
+    L = N  # parity-packed correlation of n/2 complex points, padded to n
+    flops = sum(flops_per_vector(plans32[k].K, L) * BATCH for k in KINDS) * args.steps
+    achieved = flops / (total_ms / 1e3) / 1e12
+    clocks = sampler.summary()
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FFMA lanes x 2 flop x max SM clock
+    hbm = peaks.get("hbm_gbs", 6649.7)
+    hbm_achieved = 8.0 * coeffs_per_step * args.steps / (total_ms / 1e3) / 1e9
+
+    # accuracy of the timed outputs against the oracle (sampled rows)
+    err = {}
+    if rank == 0:
+        rng = np.random.default_rng(3)
+        rows = np.unique(np.r_[np.arange(16), N - 1 - np.arange(16), rng.integers(0, N, 32)])
+        for k in KINDS:
+            err[k] = oracle_error(alpha, ys[k].double().cpu().numpy(), k, [0, BATCH - 1], rows)
+
+    # plain float64 path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        plans64 = {k: tdh.Plan(k, N, prec="fp64", tol=TOL64[k]) for k in KINDS}
+        x64 = {k: torch.tensor(alpha, dtype=torch.float64, device="cuda") for k in KINDS}
+        y64 = {k: torch.empty_like(x64[k]) for k in KINDS}
+        step(plans64, x64, y64)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        ms64 = 0.0
+        for i in range(reps):
+            flush.fill_(i)
+            e0.record(stream)
+            step(plans64, x64, y64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 += e0.elapsed_time(e1)
+        err64 = {}
+        if rank == 0:
+            for k in KINDS:
+                err64[k] = oracle_error(alpha, y64[k].cpu().numpy(), k, [0, BATCH - 1], rows)
+        fp64 = {"value": world * coeffs_per_step * reps / (ms64 / 1e3), "unit": "coeffs/s",
+                "ms_per_step": ms64 / reps, "K": {k: plans64[k].K for k in KINDS},
+                "tol": TOL64, "error_vs_oracle": err64}
+        del plans64, x64, y64
+
+    # end to end through the public API: pinned host in, host out, every step
+    hx = {k: alpha.astype(np.float32) for k in KINDS}
+    hin = {k: torch.from_numpy(hx[k]).pin_memory() for k in KINDS}
+    hout = {k: torch.empty_like(hin[k]).pin_memory() for k in KINDS}
+    for _ in range(2):
+        for k in KINDS:
+            plans32[k].execute(hin[k], out=hout[k])
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, args.steps // 2)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for k in KINDS:
+            plans32[k].execute(hin[k], out=hout[k])
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value = world * coeffs_per_step * e2e_steps / (e2e_ms / 1e3)
+    io_bytes = len(KINDS) * BATCH * N * 4
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value, "unit": "coeffs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "batch_per_gpu": BATCH, "kinds": list(KINDS),
+                       "decay": DECAY, "K": {k: plans32[k].K for k in KINDS}, "tol": TOL32,
+                       "plan_ms": plan_ms, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}, no collective"},
+            "error_vs_oracle": err,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": profile_traffic(),
+                         "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)"},
+            "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
+                    "note": "8 algorithmic bytes per coefficient (fp32 in + out); of measured"},
+            "fp64": fp64,
+            "e2e": {"value": e2e_value, "unit": "coeffs/s", "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": len(KINDS) * args.steps,
+            "kernel_ms": {"leg2cheb": statistics.mean(t_l2c), "cheb2leg": statistics.mean(t_c2l)},
+            "wall_s": wall,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
