@@ -141,6 +141,23 @@ int tdh_symbols(int kind, int64_t n, const double* p, double* t, double* h, doub
 int tdh_pchol(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, double* u,
               int64_t* pivots, int64_t* K, void* stream);
 
+/*
+ * tdh_pchol_noalloc -- tdh_pchol without any device allocation.  The paper has no
+ * counterpart; this entry point exists for callers that may not call cudaMalloc (for
+ * example code running where a caching allocator owns all device memory, or inside an
+ * allocation-free section).  Same arguments, results and errors as tdh_pchol, with:
+ *   - scratch from one static device array inside the library, sized for n <= 65536
+ *     (about 0.5 MB, held by every GPU that loads the library until the process exits);
+ *     n > 65536 returns TDH_ERR_INVALID_ARG with a message;
+ *   - no cudaMalloc / cudaFree or allocating library call;
+ *   - the first call on a device (with that device current) looks up the array's address
+ *     and caches it; make that first call before any stream capture;
+ *   - all calls on a device share the array: calls whose GPU work overlaps (other streams or
+ *     host threads) race and must be serialised by the caller.
+ */
+int tdh_pchol_noalloc(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax,
+                      double* u, int64_t* pivots, int64_t* K, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "NOMEM", -4: "ALIGN
 
 # Every entry point include/tdh.h declares (checked by the CPU test suite).
 EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "tdh_plan_query",
-           "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol")
+           "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol", "tdh_pchol_noalloc")
 
 
 class TdhError(RuntimeError):
@@ -62,6 +62,7 @@ def lib():
         L.tdh_last_error.restype = ctypes.c_char_p
         L.tdh_symbols.argtypes = [ctypes.c_int, i64, ctypes.POINTER(dbl), vp, vp, vp, vp, vp]
         L.tdh_pchol.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
+        L.tdh_pchol_noalloc.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
         for name in EXPORTS:
             if name != "tdh_last_error":
                 getattr(L, name).restype = ctypes.c_int

@@ -14,7 +14,9 @@
 // step reduces (a few hundred entries) to find the next pivot.  Every block takes the same
 // stop decision from the same data, so no grid-wide wait is needed.  The host reads the
 // "done" flag every few steps and stops launching.
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "tdh_internal.cuh"
 
@@ -214,4 +216,112 @@ extern "C" int tdh_pchol(const double* h, int64_t n, int64_t j0, double tol, int
         return TDH_ERR_INVALID_ARG;
     }
     return tdh::pchol_run(h, n, j0, tol, kmax, u, pivots, K, tdh::as_stream(stream));
+}
+
+// ----------------------------------------------------------------------------------------
+// Allocation-free pivoted Cholesky.
+//
+// Some callers cannot call cudaMalloc at all: code that runs while a caching allocator owns
+// the device memory and forbids outside allocations, or inside allocation-free real-time
+// sections.  This variant runs the same kernels as tdh_pchol but takes its scratch (the
+// residual diagonal, the per-block argmax partials and the stop state) from one statically
+// sized device array that lives in this file.  The array is part of the library image: every
+// GPU that loads the library holds it until the process exits.
+//
+// Set-up: the first call on a device (with that device current) looks up the array's device
+// address with cudaGetSymbolAddress and caches it per device; make that first call before any
+// stream capture.  All calls on a device share the one array and it keeps the contents of the
+// last call: the state words that must start at zero are cleared by every call, the rest is
+// fully rewritten.  Two calls whose work overlaps on the GPU (different streams, or different
+// host threads) race on the array; serialise them.
+namespace tdh {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 65536;
+constexpr int kNoAllocMaxParts = (int)((kNoAllocMaxN + kThreads - 1) / kThreads);
+constexpr size_t kNoAllocDBytes = sizeof(double) * (size_t)kNoAllocMaxN;
+constexpr size_t kNoAllocPartBytes = sizeof(ArgMax) * 2 * (size_t)kNoAllocMaxParts;
+constexpr size_t kNoAllocBytes = kNoAllocDBytes + kNoAllocPartBytes + 256;
+
+static __device__ __align__(256) unsigned char g_pchol_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+int noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    TDH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("tdh_pchol_noalloc: device index %d out of range", dev);
+        return TDH_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_pchol_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("tdh_pchol_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return TDH_ERR_CUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    return TDH_OK;
+}
+
+}  // namespace
+}  // namespace tdh
+
+extern "C" int tdh_pchol_noalloc(const double* h, int64_t n, int64_t j0, double tol,
+                                 int64_t kmax, double* u, int64_t* pivots, int64_t* K,
+                                 void* stream) {
+    using namespace tdh;
+    clear_error();
+    if (n < 1 || (j0 != 0 && j0 != 1) || j0 >= n || !(tol > 0.0) || kmax < 1 || !h || !u ||
+        !pivots || !K) {
+        set_error("tdh_pchol_noalloc: need n >= 1, j0 in {0,1} < n, tol > 0, kmax >= 1, non-NULL");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (n > kNoAllocMaxN) {
+        set_error("tdh_pchol_noalloc: n = %lld exceeds the static scratch limit of %lld "
+                  "coefficients; use tdh_pchol", (long long)n, (long long)kNoAllocMaxN);
+        return TDH_ERR_INVALID_ARG;
+    }
+    unsigned char* base = nullptr;
+    TDH_TRY(noalloc_scratch(&base));
+    cudaStream_t s = as_stream(stream);
+    double* d = reinterpret_cast<double*>(base);
+    ArgMax* part = reinterpret_cast<ArgMax*>(base + kNoAllocDBytes);
+    State* st = reinterpret_cast<State*>(base + kNoAllocDBytes + kNoAllocPartBytes);
+    if (kmax > kKmaxShared) kmax = kKmaxShared;
+    if (kmax > n - j0) kmax = n - j0;
+    const int nblk = (int)std::max<int64_t>(1, (n + kThreads - 1) / kThreads);
+    State host{0.0, 0, 0};
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
+    if (e == cudaSuccess) {
+        pchol_init<<<nblk, kThreads, 0, s>>>(h, n, j0, d, part);
+        e = cudaGetLastError();
+    }
+    for (int64_t r = 0; e == cudaSuccess && r < kmax; ++r) {
+        pchol_step<<<nblk, kThreads, 0, s>>>(h, n, j0, tol, (int)r, u, pivots, d,
+                                             part + (r & 1) * nblk, part + ((r + 1) & 1) * nblk,
+                                             nblk, st);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && ((r & 7) == 7 || r + 1 == kmax)) {
+            e = cudaMemcpyAsync(&host, st, sizeof(State), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess && host.done) break;
+        }
+    }
+    if (e == cudaSuccess) {
+        e = cudaMemcpyAsync(&host, st, sizeof(State), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        set_error("tdh_pchol_noalloc: %s", cudaGetErrorString(e));
+        return TDH_ERR_CUDA;
+    }
+    *K = host.K;
+    return TDH_OK;
 }
