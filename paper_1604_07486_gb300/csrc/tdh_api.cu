@@ -65,6 +65,7 @@ void release_step(Step& st) {
 // Build one conversion step: symbols (a1), pivoted Cholesky (a2), execute tables (a3).
 int build_step(Step& st, double tol, int64_t kmax, int prec, cudaStream_t s) {
     const int64_t n = st.n;
+    if (st.banded_M > 0) return TDH_OK;  // sparse factors need no plan data
     TDH_TRY(dev_alloc_t(&st.t, n));
     TDH_TRY(dev_alloc_t(&st.h, 2 * n - 1));
     TDH_TRY(dev_alloc_t(&st.d1, n));
@@ -131,11 +132,34 @@ int run(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream,
         return TDH_ERR_ALIAS;
     }
     cudaStream_t s = as_stream(stream);
-    if (plan->steps.size() != 1) {
-        set_error("multi-step plans are not built in this version");
-        return TDH_ERR_UNSUPPORTED;
+    const size_t nsteps = plan->steps.size();
+    if (nsteps == 0) {  // identity conversion (same basis)
+        TDH_CUDA(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, s));
+        return TDH_OK;
     }
-    return exec_launch(plan->steps[0], plan->params.prec, in, out, batch, adjoint, s);
+    // A = A_m ... A_1: the first step reads `in`, later steps work in place on `out` (each
+    // cluster reads its whole vector before writing it); A^T runs the steps in reverse.
+    for (size_t i = 0; i < nsteps; ++i) {
+        const Step& st = plan->steps[adjoint ? nsteps - 1 - i : i];
+        if (st.banded_M > 0) {
+            // the tiled sparse-factor kernel reads a halo from neighbouring tiles: out of place
+            if (i != 0) {
+                set_error("this chain's transpose would apply sparse factors in place "
+                          "(not built)");
+                return TDH_ERR_UNSUPPORTED;
+            }
+            TDH_TRY(banded_launch(plan->params.prec, in, out, st.n, batch, st.banded_lam0,
+                                  st.banded_M, adjoint, s));
+            continue;
+        }
+        TDH_TRY(exec_launch(st, plan->params.prec, i == 0 ? in : out, out, batch, adjoint, s));
+    }
+    return TDH_OK;
+}
+
+bool case2(double a, double b, double g) {
+    // Sec. 5.3 Case 2: |a - g| < 1, a != g, a + b > -1
+    return std::fabs(a - g) < 1.0 && a != g && a + b > -1.0;
 }
 
 }  // namespace
@@ -172,8 +196,16 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         return TDH_ERR_INVALID_ARG;
     }
     if (kind == TDH_JAC2JAC) {
-        set_error("Jacobi conversion is not built in this version");
-        return TDH_ERR_UNSUPPORTED;
+        const double a = params->p[0], b = params->p[1], g = params->p[2], d = params->p[3];
+        if (!(a > -1.0) || !(b > -1.0) || !(g > -1.0) || !(d > -1.0)) {
+            set_error("Jacobi parameters must be > -1");
+            return TDH_ERR_INVALID_ARG;
+        }
+        if ((b != d && !case2(b, a, d)) || (a != g && !case2(a, d, g))) {
+            set_error("Jacobi conversion is built for chains of Case-2 steps only "
+                      "(|b-d| < 1 with a+b > -1, and |a-g| < 1 with a+d > -1)");
+            return TDH_ERR_UNSUPPORTED;
+        }
     }
     if (kind == TDH_ULTRA2ULTRA) {
         double l1 = params->p[0], l2 = params->p[1];
@@ -181,9 +213,9 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
             set_error("ultraspherical parameters must be > 0");
             return TDH_ERR_INVALID_ARG;
         }
-        double d = l1 - l2;
-        if (!(std::fabs(d) < 1.0) || d == 0.0) {
-            set_error("ultraspherical conversion is built for 0 < |l1 - l2| < 1 only");
+        if (l1 - l2 >= 1.0) {
+            set_error("ultraspherical conversion to a smaller parameter by 1 or more needs "
+                      "back-substitution (not built)");
             return TDH_ERR_UNSUPPORTED;
         }
     }
@@ -206,12 +238,65 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         delete plan;
         return TDH_ERR_CUDA;
     }
-    Step st;
-    st.kind = kind;
-    st.n = n_max;
-    std::memcpy(st.p, params->p, sizeof(st.p));
-    plan->steps.push_back(st);
-    rc = build_step(plan->steps.back(), tol, kmax, params->prec, s);
+    if (kind == TDH_JAC2JAC) {
+        // Sec. 5.3: with b != d, reflect (P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x)), convert the
+        // first parameter b -> d, reflect back; then convert a -> g at fixed d.
+        const double a = params->p[0], b = params->p[1], g = params->p[2], d = params->p[3];
+        if (b != d) {
+            Step st;
+            st.kind = kind;
+            st.n = n_max;
+            st.full = 1;
+            st.sign_in = st.sign_out = 1;
+            st.p[0] = b;
+            st.p[1] = a;
+            st.p[2] = d;
+            plan->steps.push_back(st);
+        }
+        if (a != g) {
+            Step st;
+            st.kind = kind;
+            st.n = n_max;
+            st.full = 1;
+            st.p[0] = a;
+            st.p[1] = d;
+            st.p[2] = g;
+            plan->steps.push_back(st);
+        }
+    } else if (kind == TDH_ULTRA2ULTRA) {
+        // Sec. 5.2: Case 1 (l2 - l1 a positive integer): sparse factors only; Case 3
+        // (l2 - l1 > 1, not an integer): raise l1 by whole steps with the sparse factors,
+        // then Case 2 (|l1 - l2| < 1) with the Toeplitz-dot-Hankel product.
+        double l1 = params->p[0], l2 = params->p[1];
+        const double up = std::floor(l2 - l1);
+        if (up >= 1.0) {
+            Step st;
+            st.kind = kind;
+            st.n = n_max;
+            st.banded_M = (int)up;
+            st.banded_lam0 = l1;
+            plan->steps.push_back(st);
+            l1 += up;
+        }
+        if (l1 != l2) {
+            Step st;
+            st.kind = kind;
+            st.n = n_max;
+            st.p[0] = l1;
+            st.p[1] = l2;
+            plan->steps.push_back(st);
+        }
+    } else {
+        Step st;
+        st.kind = kind;
+        st.n = n_max;
+        std::memcpy(st.p, params->p, sizeof(st.p));
+        plan->steps.push_back(st);
+    }
+    for (auto& st : plan->steps) {
+        rc = build_step(st, tol, kmax, params->prec, s);
+        if (rc != TDH_OK) break;
+    }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (rc != TDH_OK) {

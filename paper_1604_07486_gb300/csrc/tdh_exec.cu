@@ -65,11 +65,12 @@ __device__ __forceinline__ double2 from_d2<double2>(double2 z) {
     return z;
 }
 
-// symbol of the packed correlation: s_i = t_{2i} for i < m, zero-padded to L
-__global__ void k_fill_symbol(const double* __restrict__ t, int64_t m, int64_t L,
+// symbol of the packed correlation: s_i = t_{stride i} for i < m, zero-padded to L
+// (stride 2 for parity packing, 1 for rank-pair packing)
+__global__ void k_fill_symbol(const double* __restrict__ t, int64_t m, int64_t L, int stride,
                               double2* __restrict__ x) {
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i < L) x[i] = make_double2(i < m ? t[2 * i] : 0.0, 0.0);
+    if (i < L) x[i] = make_double2(i < m ? t[stride * i] : 0.0, 0.0);
 }
 
 // one radix-2 Stockham stage (natural order in and out), float64
@@ -139,6 +140,26 @@ __global__ void k_u_gather(const double* __restrict__ u, int64_t n, int64_t K, i
     out[i] = v;
 }
 
+// rank-pair packing: out[rp][k1][k2] = (u[2rp][a], u[2rp+1][a]), a = k1 + C k2
+template <typename T>
+__global__ void k_u_gather_pairs(const double* __restrict__ u, int64_t n, int64_t K, int C,
+                                 int half, typename cx<T>::t* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t KP = (K + 1) / 2;
+    const int64_t total = KP * C * (int64_t)half;
+    if (i >= total) return;
+    const int64_t k2 = i % half;
+    const int64_t k1 = (i / half) % C;
+    const int64_t rp = i / ((int64_t)half * C);
+    const int64_t a = k1 + (int64_t)C * k2;
+    T x0 = (a < n) ? (T)u[(2 * rp) * n + a] : T(0);
+    T x1 = (a < n && 2 * rp + 1 < K) ? (T)u[(2 * rp + 1) * n + a] : T(0);
+    typename cx<T>::t v;
+    v.x = x0;
+    v.y = x1;
+    out[i] = v;
+}
+
 template <typename T>
 __global__ void k_cast(const double* __restrict__ in, T* __restrict__ out, int64_t count) {
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -187,7 +208,7 @@ int prepare_typed(Step& st, const Geometry& g, cudaStream_t s) {
             goto out;
         }
         // a3: S = DFT_L(s) in float64, natural order, by log2 L Stockham stages
-        k_fill_symbol<<<blocks_for(L), kThreads, 0, s>>>(st.t, m, L, x);
+        k_fill_symbol<<<blocks_for(L), kThreads, 0, s>>>(st.t, m, L, st.full ? 1 : 2, x);
         for (int64_t mm = 1; mm < L; mm *= 2) {
             k_stockham<<<blocks_for(L / 2), kThreads, 0, s>>>(x, y, L, mm);
             std::swap(x, y);
@@ -199,9 +220,12 @@ int prepare_typed(Step& st, const Geometry& g, cudaStream_t s) {
         for (int i = 1; i <= G.np() - 2; ++i)
             k_omega_table<V><<<blocks_for(G.M(i)), kThreads, 0, s>>>(
                 (V*)ex.twp + G.twoff(i), G.M(i), G.S(i), G.M(i));
-        if (st.K > 0)
+        if (st.K > 0 && !st.full)
             k_u_gather<T><<<blocks_for(st.K * C * (int64_t)(LC / 2)), kThreads, 0, s>>>(
                 st.u64, st.n, st.K, C, LC / 2, (V*)ex.u);
+        if (st.K > 0 && st.full)
+            k_u_gather_pairs<T><<<blocks_for((st.K + 1) / 2 * C * (int64_t)(LC / 2)), kThreads, 0,
+                                  s>>>(st.u64, st.n, st.K, C, LC / 2, (V*)ex.u);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
@@ -325,6 +349,10 @@ int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int a
     P.dout = static_cast<const T*>(adjoint ? st.d2x : st.d1x);
     P.row0 = static_cast<const T*>(st.row0);
     P.adjoint = adjoint;
+    P.full = st.full;
+    P.sign_in = st.sign_in;
+    P.sign_out = st.sign_out;
+    if (st.full) P.K = (st.K + 1) / 2;
     return dispatch<T>(ex.g, P, batch, s);
 }
 
@@ -332,7 +360,7 @@ int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int a
 
 int exec_prepare(Step& st, int prec, cudaStream_t s) {
     ExecData& ex = st.ex;
-    ex.m = (st.n + 1) / 2;
+    ex.m = st.full ? st.n : (st.n + 1) / 2;
     int logL = 8;
     while (((int64_t)1 << logL) < 2 * ex.m - 1) ++logL;
     if (!choose_geometry(prec, logL, &ex.g)) {

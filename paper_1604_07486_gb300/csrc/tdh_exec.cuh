@@ -69,6 +69,9 @@ struct ExecParams {
     const T* dout;  // D1 (forward) or D2 (adjoint), [n]
     const T* row0;  // row 0 applied directly (Chebyshev-to-Legendre), [n], or null
     int adjoint;
+    int full;       // 0: parity packing (x_2a, x_2a+1); 1: rank pairs (u_r, u_r+1) per index
+    int sign_in;    // multiply input coefficient k by (-1)^k (Jacobi reflection)
+    int sign_out;   // multiply output coefficient k by (-1)^k
 };
 
 // XOR swizzle of shared-memory element indices: rows of 128 bytes, column ^= row.
@@ -182,15 +185,26 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
     T r0acc = T(0);
     for (int k2 = tid; k2 < LC / 2; k2 += NT) {
         const int64_t a = (int64_t)k1 + (int64_t)C * k2;
-        const int64_t i0 = 2 * a;
         V v = mk<V>(0, 0);
-        if (i0 < n) {
-            const T x0 = in[i0];
-            const T x1 = (i0 + 1 < n) ? in[i0 + 1] : T(0);
-            const T s1 = (i0 + 1 < n) ? P.din[i0 + 1] : T(0);
-            if (P.row0 && !P.adjoint)
-                r0acc += P.row0[i0] * x0 + ((i0 + 1 < n) ? P.row0[i0 + 1] * x1 : T(0));
-            v = mk<V>(x0 * P.din[i0], x1 * s1);
+        if (P.full) {
+            // one coefficient per complex slot, duplicated for the two packed rank terms
+            if (a < n) {
+                T x = in[a];
+                if (P.sign_in && (a & 1)) x = -x;
+                const T xv = x * P.din[a];
+                v = mk<V>(xv, xv);
+            }
+        } else {
+            const int64_t i0 = 2 * a;
+            if (i0 < n) {
+                const T x0 = in[i0];
+                T x1 = (i0 + 1 < n) ? in[i0 + 1] : T(0);
+                if (P.sign_in) x1 = -x1;
+                const T s1 = (i0 + 1 < n) ? P.din[i0 + 1] : T(0);
+                if (P.row0 && !P.adjoint)
+                    r0acc += P.row0[i0] * x0 + ((i0 + 1 < n) ? P.row0[i0 + 1] * x1 : T(0));
+                v = mk<V>(x0 * P.din[i0], x1 * s1);
+            }
         }
         vbuf[k2] = v;
     }
@@ -314,8 +328,12 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) {
                 const V uu = ur[o + q * S0];
-                acc[j][q].x = fma(uu.x, x[q].x, acc[j][q].x);
-                acc[j][q].y = fma(uu.y, x[q].y, acc[j][q].y);
+                if (P.full) {
+                    acc[j][q].x = fma(uu.y, x[q].y, fma(uu.x, x[q].x, acc[j][q].x));
+                } else {
+                    acc[j][q].x = fma(uu.x, x[q].x, acc[j][q].x);
+                    acc[j][q].y = fma(uu.y, x[q].y, acc[j][q].y);
+                }
             }
         }
         __syncthreads();
@@ -330,6 +348,14 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) {
             const int64_t a = (int64_t)k1 + (int64_t)C * (o + q * S0);
+            if (P.full) {
+                if (a < n) {
+                    T b = acc[j][q].x * P.dout[a];
+                    if (P.sign_out && (a & 1)) b = -b;
+                    out[a] = b;
+                }
+                continue;
+            }
             const int64_t i0 = 2 * a;
             if (i0 < n) {
                 T b0 = acc[j][q].x * P.dout[i0];
@@ -338,6 +364,7 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
                 if (i0 + 1 < n) {
                     T b1 = acc[j][q].y * P.dout[i0 + 1];
                     if (P.row0 && P.adjoint) b1 += P.row0[i0 + 1] * g0;
+                    if (P.sign_out) b1 = -b1;
                     out[i0 + 1] = b1;
                 }
             }

@@ -82,6 +82,11 @@ struct Step {
     int64_t n = 0;
     int64_t K = 0;
     int64_t j0 = 0;
+    int full = 0;          // Toeplitz part without parity structure (Jacobi): rank-pair packing
+    int sign_in = 0;       // (-1)^k on the input (reflection step of a Jacobi chain)
+    int sign_out = 0;      // (-1)^k on the output
+    int banded_M = 0;      // > 0: Case-1 step of M sparse factors S_l, no T o H (Sec. 5.2)
+    double banded_lam0 = 0;  // first factor's l
     double* t = nullptr;   // [n]
     double* h = nullptr;   // [2n-1]
     double* d1 = nullptr;  // [n]
@@ -106,6 +111,9 @@ struct tdh_plan_s {
 };
 
 namespace tdh {
+// Case-1 sparse factors: out = S_{l0+M-1} ... S_{l0} in (or the transpose); out != in.
+int banded_launch(int prec, const void* in, void* out, int64_t n, int64_t batch, double lam0,
+                  int M, int adjoint, cudaStream_t s);
 // Build the execute configuration of `st` for precision `prec` (spectrum, twiddles, factors).
 int exec_prepare(Step& st, int prec, cudaStream_t s);
 void exec_release(ExecData& ex);

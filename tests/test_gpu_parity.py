@@ -208,3 +208,95 @@ def test_error_paths(tdh):
     y = plan.execute(x)
     torch.cuda.synchronize()
     assert torch.all(y == 0)
+
+
+# ------------------------------------------------------------------------------- Jacobi
+
+JAC_CASES = [
+    ((0.1, -0.3, 0.0, -0.3), "one Case-2 step (b = d)"),
+    ((0.1, -0.3, 0.0, 0.0), "reflection chain: (0.1,-0.3) -> (0.1,0) -> (0,0)"),
+    ((0.0, 2 ** 0.5 / 2, -0.25, 2 ** 0.5 / 2), "the paper's Fig. 6 workload"),
+    ((-0.4, -0.5, 0.25, -0.5), "near the Chebyshev weight"),
+]
+
+
+@pytest.mark.parametrize("params,desc", JAC_CASES, ids=[c[1] for c in JAC_CASES])
+@pytest.mark.parametrize("prec,tol,n", [("fp64", 1e-15, 3001), ("fp32", 1e-13, 3001),
+                                        ("fp32", 1e-13, 40000)])
+def test_jacobi(tdh, params, desc, prec, tol, n):
+    """Jacobi conversion (Sec. 5.3): no parity structure, so rank terms are packed in pairs;
+    b != d runs the reflection chain.  Dense oracle chain (pinned by exact rationals)."""
+    torch = _torch()
+    a, b, g, d = params
+    alpha = workloads.coefficients(n, 2, decay=1.5, seed=5)
+    plan = tdh.Plan("jac2jac", n, prec=prec, tol=tol, params=params)
+    y = plan.execute(torch.tensor(alpha, dtype=plan.dtype, device="cuda"))
+    torch.cuda.synchronize()
+    y = y.double().cpu().numpy()
+    rows = None if n <= 4096 else np.unique(np.r_[np.arange(64), n - 1 - np.arange(64),
+                                                  np.random.default_rng(4).integers(0, n, 128)])
+    if b == d:
+        ref = oracle.matvec(oracle.JAC, (a, b, g), alpha, rows=rows)
+    else:
+        ref = np.stack([oracle.jac2jac(v, a, b, g, d, rows=rows) for v in alpha])
+    yy = y if rows is None else y[:, rows]
+    err = (np.abs(yy - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
+    assert err <= TOL[prec], (err, plan.K)
+
+
+def test_jacobi_adjoint(tdh):
+    """The chain's adjoint runs the steps in reverse: <A a, g> = <a, A^T g>."""
+    torch = _torch()
+    n = 2000
+    plan = tdh.Plan("jac2jac", n, prec="fp64", tol=1e-15, params=(0.1, -0.3, 0.0, 0.0))
+    a = torch.tensor(workloads.coefficients(n, 1, decay=1.0, seed=6), dtype=torch.float64, device="cuda")
+    g = torch.tensor(workloads.cotangent(n, 1, seed=7), dtype=torch.float64, device="cuda")
+    lhs = float((plan.execute(a) * g).sum())
+    rhs = float((a * plan.adjoint(g)).sum())
+    assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + 1.0)
+
+
+# ------------------------------------------------------------------ ultraspherical Case 1/3
+
+@pytest.mark.parametrize("params", [(0.25, 1.25), (0.25, 2.25), (0.25, 1.75), (0.6, 3.1)],
+                         ids=["case1", "case1_two_factors", "case3", "case3_two_steps"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ultraspherical_case1_case3(tdh, params, prec):
+    """Sec. 5.2 Case 1 (sparse factors of eq. (sparseFactorization)) and Case 3 (whole steps,
+    then Case 2) against the dense oracle (eq. (UltraSconversion) covers every case)."""
+    n = 4099
+    tol = 1e-15 if prec == "fp64" else 1e-8
+    plan, alpha, y = _run(tdh, "ultra2ultra", n, 3, prec, tol, decay=1.5, params=params)
+    ref = oracle.matvec(oracle.ULTRA, params, alpha)
+    assert _rel_err(y, ref, alpha) <= TOL[prec]
+
+
+def test_ultraspherical_case1_adjoint(tdh):
+    torch = _torch()
+    n = 3000
+    plan = tdh.Plan("ultra2ultra", n, prec="fp64", params=(0.25, 2.25))
+    g = workloads.cotangent(n, 2, seed=3)
+    atg = plan.adjoint(torch.tensor(g, device="cuda")).cpu().numpy()
+    ref = oracle.matvec(oracle.ULTRA, (0.25, 2.25), g, transpose=True)
+    assert _rel_err(atg, ref, g) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_config4_ultraspherical_n2p20_b16(tdh, prec):
+    """C^(0.25) -> C^(1.25) at n = 2^20, batch 16, alpha_k = z_k (k+1)^-1.5: sampled rows of
+    every vector against the oracle (Case 1: one sparse factor)."""
+    n, batch = 1 << 20, 16
+    plan, alpha, y = _run(tdh, "ultra2ultra", n, batch, prec, 1e-13, decay=1.5, params=(0.25, 1.25))
+    rows = np.unique(np.r_[np.arange(64), n - 1 - np.arange(64),
+                           np.random.default_rng(8).integers(0, n, 256)])
+    ref = oracle.matvec(oracle.ULTRA, (0.25, 1.25), alpha, rows=rows)
+    err = (np.abs(y[:, rows] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
+    assert err <= TOL[prec]
+
+
+def test_jacobi_case3_reported_unsupported(tdh):
+    """a + b <= -1 (Case 3) and |a - g| > 1 (Case 4) are not built: a clear error, no result."""
+    for params in [(-0.5, -0.5, 0.25, -0.5), (0.1, 0.0, 1.6, 0.0)]:
+        with pytest.raises(tdh.TdhError) as e:
+            tdh.Plan("jac2jac", 100, params=params)
+        assert e.value.code == -2
