@@ -21,7 +21,7 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
         g->logLC = cap;
         g->C = 1 << (logL - cap);
     }
-    if (g->C > 8) return false;
+    if (g->C > 512) return false;  // C > 8: multi-pass through global memory
     if (prec == TDH_FP32)
         g->R = (g->logLC <= 9) ? 8 : 16;
     else
@@ -30,18 +30,6 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
     return true;
 }
 
-// Natural frequency of local position pos after the DIF passes (digit reversal).
-int local_freq(const PassGeom& G, int pos) {
-    int rem = pos, f = 0, mult = 1;
-    for (int i = 0; i < G.np(); ++i) {
-        const int s = G.S(i);
-        const int p = rem / s;
-        rem %= s;
-        f += p * mult;
-        mult *= G.rad(i);
-    }
-    return f;
-}
 
 constexpr int kThreads = 256;
 inline unsigned blocks_for(int64_t count) { return (unsigned)((count + kThreads - 1) / kThreads); }
@@ -117,6 +105,13 @@ template <typename V>
 __global__ void k_omega_lin(V* __restrict__ out, int64_t count, int64_t den) {
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i < count) out[i] = from_d2<V>(omega(i, den));
+}
+
+// out[i] = omega_den^{i * mult}
+template <typename V>
+__global__ void k_omega_scaled(V* __restrict__ out, int64_t count, int64_t mult, int64_t den) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < count) out[i] = from_d2<V>(omega(i * mult, den));
 }
 
 // u_dec[r][k1][k2] = (u[r][2a], u[r][2a+1]), a = k1 + C k2 (zero beyond n)
@@ -198,7 +193,14 @@ int prepare_typed(Step& st, const Geometry& g, cudaStream_t s) {
         goto out;
     ex.twp_len = G.twp_len();
     if (ex.twp_len > 0 && (rc = dev_alloc(&ex.twp, sizeof(V) * (size_t)ex.twp_len))) goto out;
-    if (C > 1 && (rc = dev_alloc(&ex.twx, sizeof(V) * (size_t)LC))) goto out;
+    ex.multipass = C > 8;
+    if (C > 1 && !ex.multipass && (rc = dev_alloc(&ex.twx, sizeof(V) * (size_t)LC))) goto out;
+    if (ex.multipass) {
+        ex.twl_shift = (g.logL + 1) / 2;
+        if ((rc = dev_alloc(&ex.twl_hi, sizeof(V) * (size_t)(L >> ex.twl_shift))) ||
+            (rc = dev_alloc(&ex.twl_lo, sizeof(V) * ((size_t)1 << ex.twl_shift))))
+            goto out;
+    }
     {
         cudaError_t e = cudaMemcpyAsync(perm_d, perm.data(), sizeof(int) * LC,
                                         cudaMemcpyHostToDevice, s);
@@ -215,7 +217,13 @@ int prepare_typed(Step& st, const Geometry& g, cudaStream_t s) {
         }
         k_spec<V><<<blocks_for((int64_t)LC * C), kThreads, 0, s>>>(x, perm_d, LC, C, L,
                                                                    (V*)ex.spec);
-        if (C > 1) k_twx<V><<<blocks_for(LC), kThreads, 0, s>>>(perm_d, LC, L, (V*)ex.twx);
+        if (C > 1 && !ex.multipass)
+            k_twx<V><<<blocks_for(LC), kThreads, 0, s>>>(perm_d, LC, L, (V*)ex.twx);
+        if (ex.multipass) {
+            const int64_t nhi = L >> ex.twl_shift, nlo = (int64_t)1 << ex.twl_shift;
+            k_omega_scaled<V><<<blocks_for(nhi), kThreads, 0, s>>>((V*)ex.twl_hi, nhi, nlo, L);
+            k_omega_scaled<V><<<blocks_for(nlo), kThreads, 0, s>>>((V*)ex.twl_lo, nlo, 1, L);
+        }
         k_omega_lin<V><<<blocks_for(LC / g.R), kThreads, 0, s>>>((V*)ex.tw0, LC / g.R, LC);
         for (int i = 1; i <= G.np() - 2; ++i)
             k_omega_table<V><<<blocks_for(G.M(i)), kThreads, 0, s>>>(
@@ -237,7 +245,10 @@ out:
     if (x || y || perm_d) cudaStreamSynchronize(s);
     dev_free(x);
     dev_free(y);
-    dev_free(perm_d);
+    if (rc == TDH_OK && ex.multipass)
+        ex.perm = perm_d;  // the multi-pass exchange kernel maps positions to frequencies
+    else
+        dev_free(perm_d);
     return rc;
 }
 
@@ -377,6 +388,9 @@ int exec_prepare(Step& st, int prec, cudaStream_t s) {
 }
 
 void exec_release(ExecData& ex) {
+    dev_free(ex.perm);
+    dev_free(ex.twl_hi);
+    dev_free(ex.twl_lo);
     dev_free(ex.spec);
     dev_free(ex.twx);
     dev_free(ex.tw0);
@@ -387,6 +401,7 @@ void exec_release(ExecData& ex) {
 
 int exec_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
                 cudaStream_t s) {
+    if (st.ex.multipass) return mp_launch(st, prec, in, out, batch, adjoint, s);
     if (prec == TDH_FP32) return launch_typed<float>(st, in, out, batch, adjoint, s);
     return launch_typed<double>(st, in, out, batch, adjoint, s);
 }

@@ -53,6 +53,19 @@ struct PassGeom {
     __host__ __device__ constexpr int twp_len() const { return twoff(np() - 1); }
 };
 
+// Natural frequency of local position pos after the DIF passes (digit reversal).
+__host__ __device__ inline int local_freq(const PassGeom& G, int pos) {
+    int rem = pos, f = 0, mult = 1;
+    for (int i = 0; i < G.np(); ++i) {
+        const int s = G.S(i);
+        const int p = rem / s;
+        rem %= s;
+        f += p * mult;
+        mult *= G.rad(i);
+    }
+    return f;
+}
+
 template <typename T>
 struct ExecParams {
     using V = typename cx<T>::t;

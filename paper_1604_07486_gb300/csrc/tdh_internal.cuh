@@ -73,6 +73,12 @@ struct ExecData {
     void* twp = nullptr;  // later-pass twiddle tables, concatenated [p][o] blocks
     int64_t twp_len = 0;  // complex entries in twp
     void* u = nullptr;    // [K][C][LC/2] complex: factors decimated by C (packed pairs)
+    // multi-pass execution (C above the cluster limit: exchange through global memory)
+    int multipass = 0;
+    int* perm = nullptr;     // [LC] natural frequency of each local position
+    void* twl_hi = nullptr;  // omega_L^{i << twl_shift}
+    void* twl_lo = nullptr;  // omega_L^{i}, i < 2^twl_shift
+    int twl_shift = 0;
 };
 
 // One T o H conversion step of a plan.
@@ -117,6 +123,9 @@ int banded_launch(int prec, const void* in, void* out, int64_t n, int64_t batch,
 // Build the execute configuration of `st` for precision `prec` (spectrum, twiddles, factors).
 int exec_prepare(Step& st, int prec, cudaStream_t s);
 void exec_release(ExecData& ex);
+// Multi-pass execute of one step (FFT longer than one cluster's shared memory).
+int mp_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
+              cudaStream_t s);
 // beta = A alpha (adjoint = 0) or A^T g (adjoint = 1) for one step.
 int exec_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
                 cudaStream_t s);

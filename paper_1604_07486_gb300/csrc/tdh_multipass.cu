@@ -1,0 +1,402 @@
+// Multi-pass execute for FFT lengths beyond one thread-block cluster (L = C * LC, C > 8):
+// the same decomposition as the cluster kernel, with the cross-CTA stage done through
+// global memory between kernel launches instead of distributed shared memory.
+//
+// Per vector b and local slice k1 (z[k1 + C k2], k2 < LC), per rank term r:
+//   mp_fwd   : u_r o v (v staged once in global memory), forward local DIF passes in
+//              shared memory, local spectrum -> Y[b][k1][pos]
+//   mp_cross : for every local position pos, the C values Y[b][*][pos]: twiddle
+//              omega_L^{k1 f1(pos)}, C-point DFT, multiply by conj(S)/L, inverse C-point
+//              DFT, conjugate twiddle (one warp per position, radix-2 in shared memory)
+//   mp_inv   : inverse local DIT passes, W[b][k1][k2] += u_r o y
+// then beta = D1 W (D2 for the adjoint).  Scratch (v, Y, W) is stream-ordered
+// (cudaMallocAsync) and vectors are processed in chunks that bound it.
+#include <algorithm>
+#include <mutex>
+
+#include "tdh_exec.cuh"
+
+namespace tdh {
+namespace {
+
+template <typename T>
+struct MPParams {
+    using V = typename cx<T>::t;
+    const T* in;
+    T* out;
+    int64_t n, L, K;
+    int C, logC, shift, adjoint, full, sign_in, sign_out;
+    const V* u;
+    const V* spec;
+    const int* perm;
+    const V* thi;
+    const V* tlo;
+    const V* tw0;
+    const V* twp;
+    const T* din;
+    const T* dout;
+    const T* row0;
+    V* vdec;  // [B][C][LC/2]
+    V* Y;     // [B][C][LC]
+    V* W;     // [B][C][LC/2]
+    T* r0;    // [B] row-0 sum (forward) or g_0 (adjoint)
+};
+
+constexpr int kEw = 256;
+
+template <typename V>
+__device__ __forceinline__ V omega_L(const V* thi, const V* tlo, int64_t e, int64_t L, int shift) {
+    e &= (L - 1);
+    return cmul(thi[e >> shift], tlo[e & (((int64_t)1 << shift) - 1)]);
+}
+
+// v in the decimated packed layout; W = 0; row-0 data
+template <typename T, int LC>
+__global__ void mp_load(const MPParams<T> P, int64_t b0, int64_t nb) {
+    using V = typename cx<T>::t;
+    const int64_t per = (int64_t)P.C * (LC / 2);
+    const int64_t total = nb * per;
+    for (int64_t i = (int64_t)blockIdx.x * kEw + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * kEw) {
+        const int64_t bl = i / per, rem = i % per;
+        const int64_t k1 = rem / (LC / 2), k2 = rem % (LC / 2);
+        const int64_t a = k1 + (int64_t)P.C * k2;
+        const T* in = P.in + (b0 + bl) * P.n;
+        V v = mk<V>(0, 0);
+        if (P.full) {
+            if (a < P.n) {
+                T x = in[a];
+                if (P.sign_in && (a & 1)) x = -x;
+                v = mk<V>(x * P.din[a], x * P.din[a]);
+            }
+        } else {
+            const int64_t i0 = 2 * a;
+            if (i0 < P.n) {
+                T x1 = (i0 + 1 < P.n) ? in[i0 + 1] : T(0);
+                if (P.sign_in) x1 = -x1;
+                v = mk<V>(in[i0] * P.din[i0], (i0 + 1 < P.n) ? x1 * P.din[i0 + 1] : T(0));
+            }
+        }
+        P.vdec[i] = v;
+        P.W[i] = mk<V>(0, 0);
+    }
+}
+
+// forward: r0[b] = sum_k row0[k] alpha_k; adjoint: r0[b] = g_0
+template <typename T>
+__global__ void mp_row0(const MPParams<T> P, int64_t b0) {
+    __shared__ T red[kEw / 32];
+    const T* in = P.in + (b0 + blockIdx.x) * P.n;
+    if (P.adjoint) {
+        if (threadIdx.x == 0) P.r0[blockIdx.x] = in[0];
+        return;
+    }
+    T acc = T(0);
+    for (int64_t k = threadIdx.x; k < P.n; k += kEw) {
+        T x = in[k];
+        if (P.sign_in && (k & 1)) x = -x;
+        acc += P.row0[k] * x;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T s = T(0);
+        for (int w = 0; w < kEw / 32; ++w) s += red[w];
+        P.r0[blockIdx.x] = s;
+    }
+}
+
+template <typename T, int LOGLC, int R, int NT>
+__global__ void __launch_bounds__(NT, 1) mp_fwd(const MPParams<T> P, int64_t r) {
+    using V = typename cx<T>::t;
+    constexpr PassGeom G{LOGLC, R};
+    constexpr int LC = G.LC(), S0 = LC / R, J0 = S0 / NT, RL = G.rad(G.np() - 1);
+    constexpr int TWP = G.twp_len();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* buf = reinterpret_cast<V*>(smem_raw);
+    V* twt = buf + LC;
+    const int tid = threadIdx.x;
+    const int64_t bl = blockIdx.x / P.C;
+    const int k1 = blockIdx.x % P.C;
+    for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
+    const V* vs = P.vdec + (bl * P.C + k1) * (LC / 2);
+    const V* ur = P.u + (r * P.C + k1) * (LC / 2);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < J0; ++j) {
+        const int o = tid + j * NT;
+        V x[R];
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) x[q] = cwmul(vs[o + q * S0], ur[o + q * S0]);
+        dif_halfzero<R>(x);
+        V wp[R];
+        powers<R>(P.tw0[o], wp);
+#pragma unroll
+        for (int jj = 0; jj < R; ++jj) {
+            const int p = bitrev(jj, R);
+            buf[swz<V>(o + p * S0)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
+        }
+    }
+    __syncthreads();
+    middle_fwd<1, LOGLC, R, NT>(buf, twt);
+#pragma unroll 1
+    for (int g = tid; g < LC / RL; g += NT) {
+        V x[RL];
+#pragma unroll
+        for (int q = 0; q < RL; ++q) x[q] = buf[swz<V>(g * RL + q)];
+        dif<RL>(x);
+#pragma unroll
+        for (int jj = 0; jj < RL; ++jj) buf[swz<V>(g * RL + bitrev(jj, RL))] = x[jj];
+    }
+    __syncthreads();
+    V* y = P.Y + (bl * P.C + k1) * LC;
+    for (int pos = tid; pos < LC; pos += NT) y[pos] = buf[swz<V>(pos)];
+}
+
+template <typename T, int LOGLC, int R, int NT>
+__global__ void __launch_bounds__(NT, 1) mp_inv(const MPParams<T> P, int64_t r) {
+    using V = typename cx<T>::t;
+    constexpr PassGeom G{LOGLC, R};
+    constexpr int LC = G.LC(), S0 = LC / R, J0 = S0 / NT, RL = G.rad(G.np() - 1);
+    constexpr int TWP = G.twp_len();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* buf = reinterpret_cast<V*>(smem_raw);
+    V* twt = buf + LC;
+    const int tid = threadIdx.x;
+    const int64_t bl = blockIdx.x / P.C;
+    const int k1 = blockIdx.x % P.C;
+    for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
+    const V* y = P.Y + (bl * P.C + k1) * LC;
+    for (int pos = tid; pos < LC; pos += NT) buf[swz<V>(pos)] = y[pos];
+    __syncthreads();
+#pragma unroll 1
+    for (int g = tid; g < LC / RL; g += NT) {
+        V x[RL];
+#pragma unroll
+        for (int p = 0; p < RL; ++p) x[bitrev(p, RL)] = buf[swz<V>(g * RL + p)];
+        dit<RL>(x);
+#pragma unroll
+        for (int q = 0; q < RL; ++q) buf[swz<V>(g * RL + q)] = x[q];
+    }
+    __syncthreads();
+    middle_inv<G.np() - 2, LOGLC, R, NT>(buf, twt);
+    const V* ur = P.u + (r * P.C + k1) * (LC / 2);
+    V* w = P.W + (bl * P.C + k1) * (LC / 2);
+#pragma unroll
+    for (int j = 0; j < J0; ++j) {
+        const int o = tid + j * NT;
+        V wp[R];
+        powers<R>(P.tw0[o], wp);
+        V x[R];
+#pragma unroll
+        for (int p = 0; p < R; ++p) {
+            const V yy = buf[swz<V>(o + p * S0)];
+            x[bitrev(p, R)] = (p == 0) ? yy : cmulc(yy, wp[p]);
+        }
+        dit_halfout<R>(x);
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) {
+            const V uu = ur[o + q * S0];
+            V acc = w[o + q * S0];
+            if (P.full) {
+                acc.x = fma(uu.y, x[q].y, fma(uu.x, x[q].x, acc.x));
+            } else {
+                acc.x = fma(uu.x, x[q].x, acc.x);
+                acc.y = fma(uu.y, x[q].y, acc.y);
+            }
+            w[o + q * S0] = acc;
+        }
+    }
+}
+
+// Cross stage: one warp per local position, C values in shared memory (padded rows).
+template <typename T, int LC>
+__global__ void __launch_bounds__(256) mp_cross(const MPParams<T> P) {
+    using V = typename cx<T>::t;
+    constexpr int PPB = 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int C = P.C, ld = C + 1;
+    V* tile = reinterpret_cast<V*>(smem_raw);  // [PPB][C + 1]
+    V* twc = tile + PPB * ld;                  // omega_C^k, k < C/2
+    const int64_t bl = blockIdx.y;
+    const int pos0 = blockIdx.x * PPB;
+    for (int k = threadIdx.x; k < C / 2; k += blockDim.x)
+        twc[k] = omega_L(P.thi, P.tlo, (int64_t)k * (P.L / C), P.L, P.shift);
+    const V* Yb = P.Y + bl * (int64_t)C * LC;
+    V* Yw = P.Y + bl * (int64_t)C * LC;
+    for (int idx = threadIdx.x; idx < PPB * C; idx += blockDim.x) {
+        const int k1 = idx / PPB, p = idx % PPB;
+        const int pos = pos0 + p;
+        const V w = omega_L(P.thi, P.tlo, (int64_t)k1 * P.perm[pos], P.L, P.shift);
+        tile[p * ld + k1] = cmul(Yb[(int64_t)k1 * LC + pos], w);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int p = warp; p < PPB; p += nw) {
+        V* x = tile + p * ld;
+        for (int h = C / 2; h >= 1; h >>= 1) {
+            for (int i = lane; i < C / 2; i += 32) {
+                const int j = i % h, i0 = (i / h) * 2 * h + j, i1 = i0 + h;
+                const V a = x[i0], c = x[i1];
+                x[i0] = cadd(a, c);
+                x[i1] = cmul(csub(a, c), twc[j * (C / (2 * h))]);
+            }
+            __syncwarp();
+        }
+        const int64_t pos = pos0 + p;
+        for (int i = lane; i < C; i += 32) {
+            const int f2 = (int)(__brev((unsigned)i) >> (32 - P.logC));
+            const V s = P.spec[pos * C + f2];
+            x[i] = P.adjoint ? cmulc(x[i], s) : cmul(x[i], s);
+        }
+        __syncwarp();
+        for (int h = 1; h <= C / 2; h <<= 1) {
+            for (int i = lane; i < C / 2; i += 32) {
+                const int j = i % h, i0 = (i / h) * 2 * h + j, i1 = i0 + h;
+                const V a = x[i0], c = cmulc(x[i1], twc[j * (C / (2 * h))]);
+                x[i0] = cadd(a, c);
+                x[i1] = csub(a, c);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < PPB * C; idx += blockDim.x) {
+        const int k1 = idx / PPB, p = idx % PPB;
+        const int pos = pos0 + p;
+        const V w = omega_L(P.thi, P.tlo, (int64_t)k1 * P.perm[pos], P.L, P.shift);
+        Yw[(int64_t)k1 * LC + pos] = cmulc(tile[p * ld + k1], w);
+    }
+}
+
+template <typename T, int LC>
+__global__ void mp_store(const MPParams<T> P, int64_t b0, int64_t nb) {
+    using V = typename cx<T>::t;
+    const int64_t per_out = P.n;
+    const int64_t total = nb * per_out;
+    for (int64_t i = (int64_t)blockIdx.x * kEw + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * kEw) {
+        const int64_t bl = i / per_out, k = i % per_out;
+        const int64_t a = P.full ? k : k / 2;
+        const int64_t k1 = a % P.C, k2 = a / P.C;
+        const V w = P.W[(bl * P.C + k1) * (LC / 2) + k2];
+        T v = (P.full || !(k & 1)) ? w.x : w.y;
+        v *= P.dout[k];
+        if (P.row0 && P.adjoint) v += P.row0[k] * P.r0[bl];
+        if (P.row0 && !P.adjoint && k == 0) v = P.r0[bl];
+        if (P.sign_out && (k & 1)) v = -v;
+        P.out[(b0 + bl) * P.n + k] = v;
+    }
+}
+
+template <typename T, int LOGLC, int R, int NT>
+int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjoint,
+              cudaStream_t s) {
+    using V = typename cx<T>::t;
+    constexpr PassGeom G{LOGLC, R};
+    constexpr int LC = G.LC();
+    const ExecData& ex = st.ex;
+    if (ex.g.logLC != LOGLC || ex.g.R != R) {
+        set_error("multi-pass geometry mismatch");
+        return TDH_ERR_UNSUPPORTED;
+    }
+    MPParams<T> P{};
+    P.in = static_cast<const T*>(in);
+    P.out = static_cast<T*>(out);
+    P.n = st.n;
+    P.C = ex.g.C;
+    P.logC = ilog2(P.C);
+    P.L = (int64_t)1 << ex.g.logL;
+    P.K = st.full ? (st.K + 1) / 2 : st.K;
+    P.shift = ex.twl_shift;
+    P.adjoint = adjoint;
+    P.full = st.full;
+    P.sign_in = st.sign_in;
+    P.sign_out = st.sign_out;
+    P.u = static_cast<const V*>(ex.u);
+    P.spec = static_cast<const V*>(ex.spec);
+    P.perm = ex.perm;
+    P.thi = static_cast<const V*>(ex.twl_hi);
+    P.tlo = static_cast<const V*>(ex.twl_lo);
+    P.tw0 = static_cast<const V*>(ex.tw0);
+    P.twp = static_cast<const V*>(ex.twp);
+    P.din = static_cast<const T*>(adjoint ? st.d1x : st.d2x);
+    P.dout = static_cast<const T*>(adjoint ? st.d2x : st.d1x);
+    P.row0 = static_cast<const T*>(st.row0);
+
+    // chunk the batch so the scratch stays below ~2 GB
+    const size_t per_vec = sizeof(V) * (size_t)P.L * 2 + sizeof(T);
+    int64_t chunk = std::max<int64_t>(1, (int64_t)((size_t)2 << 30) / (int64_t)per_vec);
+    chunk = std::min(chunk, batch);
+    char* scratch = nullptr;
+    const size_t bytes = per_vec * (size_t)chunk + 256;
+    TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s));
+    P.vdec = reinterpret_cast<V*>(scratch);
+    P.W = P.vdec + (size_t)chunk * P.L / 2;
+    P.Y = P.W + (size_t)chunk * P.L / 2;
+    P.r0 = reinterpret_cast<T*>(P.Y + (size_t)chunk * P.L);
+
+    constexpr size_t smem_pass = (size_t)(LC + G.twp_len()) * sizeof(V);
+    const size_t smem_cross = (size_t)(16 * (P.C + 1) + P.C / 2) * sizeof(V);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(mp_fwd<T, LOGLC, R, NT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pass);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(mp_inv<T, LOGLC, R, NT>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_pass);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(mp_cross<T, LC>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(V) * (16 * 513 + 256)));
+    });
+    int rc = TDH_OK;
+    if (attr_err != cudaSuccess) {
+        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(attr_err));
+        rc = TDH_ERR_CUDA;
+    }
+    for (int64_t b0 = 0; rc == TDH_OK && b0 < batch; b0 += chunk) {
+        const int64_t nb = std::min(chunk, batch - b0);
+        MPParams<T> Q = P;
+        Q.in = P.in + b0 * P.n;
+        const unsigned ew = (unsigned)std::min<int64_t>((nb * P.L / 2 + kEw - 1) / kEw, 4096);
+        mp_load<T, LC><<<ew, kEw, 0, s>>>(Q, 0, nb);
+        if (P.row0) mp_row0<T><<<(unsigned)nb, kEw, 0, s>>>(Q, 0);
+        for (int64_t r = 0; r < P.K; ++r) {
+            mp_fwd<T, LOGLC, R, NT><<<(unsigned)(nb * P.C), NT, smem_pass, s>>>(Q, r);
+            mp_cross<T, LC><<<dim3(LC / 16, (unsigned)nb), 256, smem_cross, s>>>(Q);
+            mp_inv<T, LOGLC, R, NT><<<(unsigned)(nb * P.C), NT, smem_pass, s>>>(Q, r);
+        }
+        Q.in = P.in;
+        const unsigned eo = (unsigned)std::min<int64_t>((nb * P.n + kEw - 1) / kEw, 4096);
+        mp_store<T, LC><<<eo, kEw, 0, s>>>(Q, b0, nb);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error("multi-pass launch: %s", cudaGetErrorString(e));
+            rc = TDH_ERR_CUDA;
+        }
+    }
+    cudaError_t e = cudaFreeAsync(scratch, s);
+    if (rc == TDH_OK && e != cudaSuccess) {
+        set_error("cudaFreeAsync: %s", cudaGetErrorString(e));
+        rc = TDH_ERR_CUDA;
+    }
+    return rc;
+}
+
+}  // namespace
+
+int mp_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
+              cudaStream_t s) {
+    if (st.ex.g.C > 512) {
+        set_error("multi-pass cross stage supports at most 512 slices");
+        return TDH_ERR_UNSUPPORTED;
+    }
+    if (prec == TDH_FP32) return run_typed<float, 14, 16, 512>(st, in, out, batch, adjoint, s);
+    return run_typed<double, 13, 8, 512>(st, in, out, batch, adjoint, s);
+}
+
+}  // namespace tdh

@@ -300,3 +300,98 @@ def test_jacobi_case3_reported_unsupported(tdh):
         with pytest.raises(tdh.TdhError) as e:
             tdh.Plan("jac2jac", 100, params=params)
         assert e.value.code == -2
+
+
+# ---------------------------------------------------------------- multi-pass (large L)
+
+def _rows(n, seed=4, k=64):
+    return np.unique(np.r_[np.arange(k), n - 1 - np.arange(k),
+                           np.random.default_rng(seed).integers(0, n, k)])
+
+
+@pytest.mark.parametrize("kind,prec,tol,n", [("leg2cheb", "fp64", 1e-15, 70001),
+                                             ("cheb2leg", "fp64", 1e-17, 70001),
+                                             ("leg2cheb", "fp32", 1e-7, 200001),
+                                             ("cheb2leg", "fp32", 1e-10, 200001)])
+def test_multipass_parity(tdh, kind, prec, tol, n):
+    """FFT lengths beyond one cluster (exchange through global memory): sampled rows against
+    the oracle, and the adjoint identity."""
+    torch = _torch()
+    plan, alpha, y = _run(tdh, kind, n, 2, prec, tol, decay=0.5)
+    rows = _rows(n)
+    ref = oracle.matvec(OKIND[kind], None, alpha, rows=rows)
+    err = (np.abs(y[:, rows] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
+    assert err <= TOL[prec], err
+    g = workloads.cotangent(n, 2, seed=3)
+    atg = plan.adjoint(torch.tensor(g, dtype=plan.dtype, device="cuda")).double().cpu().numpy()
+    ref = oracle.matvec(OKIND[kind], None, g, rows=rows, transpose=True)
+    err = (np.abs(atg[:, rows] - ref).max(axis=1) / np.abs(g).sum(axis=1)).max()
+    assert err <= TOL[prec], err
+
+
+def _jac_tail_oracle(alpha, params, tail):
+    """Rows j >= tail[0] of the reflection chain, exactly: upper triangularity means they only
+    involve coefficients k >= tail[0] at every step."""
+    a, b, g, d = params
+    n = alpha.shape[-1]
+    sign = (-1.0) ** np.arange(n)
+    out = []
+    for v in np.atleast_2d(alpha):
+        y = np.zeros(n)
+        y[tail] = sign[tail] * oracle.matvec(oracle.JAC, (b, a, d), sign * v, rows=tail)
+        out.append(oracle.matvec(oracle.JAC, (a, d, g), y, rows=tail))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("prec,tol,n", [("fp32", 1e-13, 70000), ("fp64", 1e-15, 40000)])
+def test_jacobi_multipass(tdh, prec, tol, n):
+    params = (0.1, -0.3, 0.0, 0.0)
+    torch = _torch()
+    alpha = workloads.coefficients(n, 2, decay=1.5, seed=5)
+    plan = tdh.Plan("jac2jac", n, prec=prec, tol=tol, params=params)
+    y = plan.execute(torch.tensor(alpha, dtype=plan.dtype, device="cuda")).double().cpu().numpy()
+    tail = np.arange(n - 1500, n)
+    ref = _jac_tail_oracle(alpha, params, tail)
+    err = (np.abs(y[:, tail] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
+    assert err <= TOL[prec], err
+    # prefix: alpha supported on [0, 4096) converts like the n = 4096 problem, zeros above
+    a2 = alpha.copy()
+    a2[:, 4096:] = 0.0
+    y2 = plan.execute(torch.tensor(a2, dtype=plan.dtype, device="cuda")).double().cpu().numpy()
+    ref2 = np.stack([oracle.jac2jac(v[:4096], *params) for v in a2])
+    err = (np.abs(y2[:, :4096] - ref2).max(axis=1) / np.abs(a2).sum(axis=1)).max()
+    assert err <= TOL[prec], err
+    assert np.abs(y2[:, 4096:]).max() <= TOL[prec] * np.abs(a2).sum(axis=1).max()
+
+
+def test_config4_jacobi_n2p20_b16(tdh):
+    """P^(0.1,-0.3) -> P^(0,0), n = 2^20, batch 16, float32 execute, float64 plan, tol 1e-13:
+    the last 1024 rows of every vector exactly against the oracle chain, and the prefix
+    property on two vectors."""
+    torch = _torch()
+    n, batch = 1 << 20, 16
+    params = (0.1, -0.3, 0.0, 0.0)
+    alpha = workloads.coefficients(n, batch, decay=1.5, seed=0)
+    plan = tdh.Plan("jac2jac", n, prec="fp32", tol=1e-13, params=params)
+    y = plan.execute(torch.tensor(alpha, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    assert np.all(np.isfinite(y))
+    tail = np.arange(n - 1024, n)
+    ref = _jac_tail_oracle(alpha, params, tail)
+    err = (np.abs(y[:, tail] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
+    assert err <= 5e-6, err
+    a2 = alpha[:2].copy()
+    a2[:, 8192:] = 0.0
+    y2 = plan.execute(torch.tensor(a2, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    ref2 = np.stack([oracle.jac2jac(v[:8192], *params) for v in a2])
+    err = (np.abs(y2[:, :8192] - ref2).max(axis=1) / np.abs(a2).sum(axis=1)).max()
+    assert err <= 5e-6, err
+
+
+def test_config4_supplementary_ultraspherical_case2_n2p20(tdh):
+    """C^(0.25) -> C^(1.0) (Case 2, the Toeplitz-dot-Hankel path) at the config-4 size."""
+    n, batch = 1 << 20, 16
+    plan, alpha, y = _run(tdh, "ultra2ultra", n, batch, "fp32", 1e-13, decay=1.5, params=(0.25, 1.0))
+    rows = _rows(n, k=48)
+    ref = oracle.matvec(oracle.ULTRA, (0.25, 1.0), alpha, rows=rows)
+    err = (np.abs(y[:, rows] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
+    assert err <= 5e-6, err
