@@ -41,7 +41,8 @@ extern "C" {
 #define TDH_FP32  1 /* float32 in/out, float32 FFT (plan factors rounded once from float64)    */
 
 /* ---------------------------------------------------------------- plan flags */
-#define TDH_FLAG_NONE 0
+#define TDH_FLAG_NONE   0
+#define TDH_FLAG_RAGGED 1 /* also prepare every shorter FFT length (tdh_plan_execute_ragged)  */
 
 /* ---------------------------------------------------------------- error codes */
 #define TDH_OK               0
@@ -89,6 +90,25 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
  * Asynchronous on `stream`; the plan may be used from several streams at once.
  */
 int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream);
+
+/*
+ * tdh_plan_execute_ragged -- beta = A alpha for `batch` vectors of different lengths in one
+ * call.  Vector v occupies in[offsets[v] .. offsets[v+1]) and its result the same range of
+ * out; its length n_v = offsets[v+1] - offsets[v] must be <= n_max (longer vectors are left
+ * unwritten; n_v = 0 is allowed).  One plan serves every length: H and T depend only on j+k
+ * and k-j, so the n_v-prefix of the n_max factors approximates the n_v problem within the same
+ * tolerance (the residual of a principal submatrix is a principal submatrix of the residual).
+ * in, out: device arrays of offsets[batch] values of the plan's precision; out must not
+ * overlap in (not checked).  offsets: device, batch + 1 int64, non-decreasing, offsets[0] >= 0.
+ * The plan must have been created with TDH_FLAG_RAGGED (else TDH_ERR_INVALID_ARG) and have a
+ * single conversion step (Legendre/Chebyshev/ultraspherical Case 2) with FFT lengths within
+ * one thread-block cluster.  Vectors are grouped by FFT length on the device; each length
+ * class is converted by one persistent launch that takes vectors from a work counter, and the
+ * classes run concurrently on plan-owned streams forked from `stream` (capturable in a CUDA
+ * graph).  Asynchronous; scratch is stream-ordered (cudaMallocAsync).
+ */
+int tdh_plan_execute_ragged(tdh_plan_t plan, const void* in, void* out, const int64_t* offsets,
+                            int64_t batch, void* stream);
 
 /*
  * tdh_plan_execute_adjoint -- grad = A^T g for `batch` vectors (the transpose product used

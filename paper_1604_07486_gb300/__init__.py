@@ -21,7 +21,9 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "NOMEM", -4: "ALIGN
 
 # Every entry point include/tdh.h declares (checked by the CPU test suite).
 EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "tdh_plan_query",
-           "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol", "tdh_pchol_noalloc")
+           "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol", "tdh_pchol_noalloc",
+           "tdh_plan_execute_ragged")
+FLAG_RAGGED = 1
 
 
 class TdhError(RuntimeError):
@@ -56,6 +58,7 @@ def lib():
                                       ctypes.POINTER(vp)]
         L.tdh_plan_execute.argtypes = [vp, vp, vp, i64, vp]
         L.tdh_plan_execute_adjoint.argtypes = [vp, vp, vp, i64, vp]
+        L.tdh_plan_execute_ragged.argtypes = [vp, vp, vp, vp, i64, vp]
         L.tdh_plan_query.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.tdh_plan_destroy.argtypes = [vp]
         L.tdh_last_error.argtypes = []
@@ -95,7 +98,7 @@ class Plan:
     """A conversion plan (tdh_plan_create): symbols, pivoted Cholesky and FFT tables for
     vectors of n coefficients, built on the current CUDA device in float64."""
 
-    def __init__(self, kind, n, prec="fp32", tol=None, params=(), kmax=0):
+    def __init__(self, kind, n, prec="fp32", tol=None, params=(), kmax=0, ragged=False):
         self.kind = _kind(kind)
         self.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
         if tol is None:
@@ -104,7 +107,7 @@ class Plan:
         for i, v in enumerate(params):
             p.p[i] = float(v)
         p.prec = self.prec
-        p.flags = 0
+        p.flags = FLAG_RAGGED if ragged else 0
         p.kmax = int(kmax)
         h = ctypes.c_void_p()
         _check(lib().tdh_plan_create(self.kind, int(n), ctypes.byref(p), float(tol),
@@ -151,6 +154,21 @@ class Plan:
         runs on `stream` (default: torch's current stream) and returns asynchronously; a CPU
         tensor is copied in, converted and copied back (synchronise before reading)."""
         return self._run(lib().tdh_plan_execute, x, out, stream)
+
+    def execute_ragged(self, x, offsets, out=None, stream=None):
+        """Convert vectors of different lengths in one call: vector v is
+        x[offsets[v]:offsets[v+1]] (CUDA tensors; offsets int64 with batch + 1 entries, every
+        length <= n).  The plan must have been made with ragged=True."""
+        torch = _torch()
+        if x.dtype != self.dtype or not x.is_contiguous() or x.device.type != "cuda":
+            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor")
+        if offsets.dtype != torch.int64 or offsets.device.type != "cuda":
+            raise ValueError("offsets must be a CUDA int64 tensor")
+        od = out if out is not None else torch.empty_like(x)
+        _check(lib().tdh_plan_execute_ragged(
+            self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(od.data_ptr()),
+            ctypes.c_void_p(offsets.data_ptr()), offsets.numel() - 1, _stream(stream)))
+        return od
 
     def adjoint(self, g, out=None, stream=None):
         """A^T g for every vector of g (the transpose product)."""

@@ -49,6 +49,9 @@ int sm_count() {
 namespace {
 
 void release_step(Step& st) {
+    for (auto& ex : st.rcls) exec_release(ex);
+    st.rcls.clear();
+    dev_free(st.u_nat);
     dev_free(st.t);
     dev_free(st.h);
     dev_free(st.d1);
@@ -297,15 +300,68 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         rc = build_step(st, tol, kmax, params->prec, s);
         if (rc != TDH_OK) break;
     }
+    if (rc == TDH_OK && (params->flags & TDH_FLAG_RAGGED)) {
+        if (plan->steps.size() != 1) {
+            set_error("ragged batches need a single-step conversion");
+            rc = TDH_ERR_UNSUPPORTED;
+        } else {
+            rc = exec_prepare_ragged(plan->steps[0], params->prec, s);
+        }
+        const size_t ncls = plan->steps.empty() ? 0 : plan->steps[0].rcls.size();
+        for (size_t i = 0; rc == TDH_OK && i < ncls; ++i) {
+            cudaStream_t ss = nullptr;
+            cudaError_t ee = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+            if (ee == cudaSuccess) plan->side.push_back(ss);
+            else rc = TDH_ERR_CUDA;
+        }
+        for (size_t i = 0; rc == TDH_OK && i < ncls + 1; ++i) {
+            cudaEvent_t ev = nullptr;
+            cudaError_t ee = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (ee == cudaSuccess) plan->ev.push_back(ev);
+            else rc = TDH_ERR_CUDA;
+        }
+        if (rc == TDH_ERR_CUDA && !tdh_last_error()[0]) set_error("stream/event creation failed");
+    }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (rc != TDH_OK) {
         for (auto& x : plan->steps) release_step(x);
+        for (auto ss : plan->side) cudaStreamDestroy(ss);
+        for (auto ev : plan->ev) cudaEventDestroy(ev);
         delete plan;
         return rc;
     }
     *out = plan;
     return TDH_OK;
+}
+
+int tdh_plan_execute_ragged(tdh_plan_t plan, const void* in, void* out, const int64_t* offsets,
+                            int64_t batch, void* stream) {
+    clear_error();
+    if (!plan) {
+        set_error("NULL plan");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch < 0) {
+        set_error("batch must be >= 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return TDH_OK;
+    if (!in || !out || !offsets) {
+        set_error("NULL in/out/offsets");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (!(plan->params.flags & TDH_FLAG_RAGGED) || plan->steps.size() != 1 ||
+        plan->steps[0].rcls.empty()) {
+        set_error("plan was not created with TDH_FLAG_RAGGED");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch > (int64_t)1 << 31) {
+        set_error("ragged batch above 2^31 vectors");
+        return TDH_ERR_UNSUPPORTED;
+    }
+    return exec_launch_ragged(plan->steps[0], plan->params.prec, in, out, offsets, batch,
+                              as_stream(stream), plan->side, plan->ev);
 }
 
 int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream) {
@@ -334,6 +390,8 @@ int tdh_plan_destroy(tdh_plan_t plan) {
     clear_error();
     if (!plan) return TDH_OK;
     for (auto& st : plan->steps) release_step(st);
+    for (auto ss : plan->side) cudaStreamDestroy(ss);
+    for (auto ev : plan->ev) cudaEventDestroy(ev);
     delete plan;
     return TDH_OK;
 }

@@ -172,13 +172,14 @@ __global__ void k_row0(const double* __restrict__ t, const double* __restrict__ 
 }
 
 template <typename T>
-int prepare_typed(Step& st, const Geometry& g, cudaStream_t s) {
+int prepare_typed(Step& st, ExecData& ex, const Geometry& g, const void* shared_u,
+                  int64_t shared_stride, cudaStream_t s) {
     using V = typename cx<T>::t;
-    ExecData& ex = st.ex;
     const PassGeom G{g.logLC, g.R};
     const int LC = G.LC(), C = g.C;
     const int64_t L = (int64_t)1 << g.logL;
-    const int64_t m = ex.m;
+    // symbol entries the correlation can touch: below m, and below L/2 so nothing wraps
+    const int64_t m = std::min<int64_t>(ex.m, L / 2);
     int rc = TDH_OK;
     double2 *x = nullptr, *y = nullptr;
     int* perm_d = nullptr;
@@ -188,9 +189,17 @@ int prepare_typed(Step& st, const Geometry& g, cudaStream_t s) {
     if ((rc = dev_alloc_t(&x, L)) || (rc = dev_alloc_t(&y, L)) || (rc = dev_alloc_t(&perm_d, LC)))
         goto out;
     if ((rc = dev_alloc(&ex.spec, sizeof(V) * (size_t)LC * C)) ||
-        (rc = dev_alloc(&ex.tw0, sizeof(V) * (size_t)(LC / g.R))) ||
-        (rc = dev_alloc(&ex.u, sizeof(V) * (size_t)std::max<int64_t>(st.K, 1) * C * (LC / 2))))
+        (rc = dev_alloc(&ex.tw0, sizeof(V) * (size_t)(LC / g.R))))
         goto out;
+    if (shared_u) {
+        ex.u = const_cast<void*>(shared_u);
+        ex.u_owned = false;
+        ex.u_stride = shared_stride;
+    } else {
+        ex.u_stride = LC / 2;
+        if ((rc = dev_alloc(&ex.u, sizeof(V) * (size_t)std::max<int64_t>(st.K, 1) * C * (LC / 2))))
+            goto out;
+    }
     ex.twp_len = G.twp_len();
     if (ex.twp_len > 0 && (rc = dev_alloc(&ex.twp, sizeof(V) * (size_t)ex.twp_len))) goto out;
     ex.multipass = C > 8;
@@ -228,10 +237,10 @@ int prepare_typed(Step& st, const Geometry& g, cudaStream_t s) {
         for (int i = 1; i <= G.np() - 2; ++i)
             k_omega_table<V><<<blocks_for(G.M(i)), kThreads, 0, s>>>(
                 (V*)ex.twp + G.twoff(i), G.M(i), G.S(i), G.M(i));
-        if (st.K > 0 && !st.full)
+        if (st.K > 0 && !st.full && !shared_u)
             k_u_gather<T><<<blocks_for(st.K * C * (int64_t)(LC / 2)), kThreads, 0, s>>>(
                 st.u64, st.n, st.K, C, LC / 2, (V*)ex.u);
-        if (st.K > 0 && st.full)
+        if (st.K > 0 && st.full && !shared_u)
             k_u_gather_pairs<T><<<blocks_for((st.K + 1) / 2 * C * (int64_t)(LC / 2)), kThreads, 0,
                                   s>>>(st.u64, st.n, st.K, C, LC / 2, (V*)ex.u);
         e = cudaGetLastError();
@@ -299,6 +308,19 @@ int launch_inst(const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
+    if (P.ragged) {
+        // persistent: as many clusters as can be resident, at most one per vector
+        int resident = 0;
+        if (C > 1) {
+            TDH_CUDA(cudaOccupancyMaxActiveClusters(&resident, kern, &cfg));
+        } else {
+            int per_sm = 0;
+            TDH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+            resident = per_sm * sm_count();
+        }
+        const int64_t nclusters = std::max<int64_t>(1, std::min<int64_t>(batch, resident));
+        cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
+    }
     TDH_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
     return TDH_OK;
 }
@@ -364,6 +386,12 @@ int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int a
     P.sign_in = st.sign_in;
     P.sign_out = st.sign_out;
     if (st.full) P.K = (st.K + 1) / 2;
+    P.u_stride = ((int64_t)1 << ex.g.logLC) / 2;
+    P.ragged = 0;
+    P.offs = nullptr;
+    P.list = nullptr;
+    P.count = nullptr;
+    P.next = nullptr;
     return dispatch<T>(ex.g, P, batch, s);
 }
 
@@ -381,13 +409,48 @@ int exec_prepare(Step& st, int prec, cudaStream_t s) {
     }
     if (prec == TDH_FP32) {
         TDH_TRY(prepare_diagonals<float>(st, s));
-        return prepare_typed<float>(st, ex.g, s);
+        return prepare_typed<float>(st, ex, ex.g, nullptr, 0, s);
     }
     TDH_TRY(prepare_diagonals<double>(st, s));
-    return prepare_typed<double>(st, ex.g, s);
+    return prepare_typed<double>(st, ex, ex.g, nullptr, 0, s);
+}
+
+namespace {
+template <typename T>
+int prepare_ragged_typed(Step& st, int prec, cudaStream_t s) {
+    using V = typename cx<T>::t;
+    const int64_t half = (st.n + 1) / 2;
+    TDH_TRY(dev_alloc(&st.u_nat, sizeof(V) * (size_t)std::max<int64_t>(st.K, 1) * half));
+    if (st.K > 0)
+        k_u_gather<T><<<blocks_for(st.K * half), kThreads, 0, s>>>(st.u64, st.n, st.K, 1,
+                                                                   (int)half, (V*)st.u_nat);
+    TDH_CUDA(cudaGetLastError());
+    for (int logL = 8; logL <= st.ex.g.logL; ++logL) {
+        st.rcls.emplace_back();
+        ExecData& ex = st.rcls.back();
+        ex.m = st.ex.m;
+        if (!choose_geometry(prec, logL, &ex.g) || ex.g.C > 8) {
+            set_error("ragged batches are built for FFT lengths within one cluster");
+            return TDH_ERR_UNSUPPORTED;
+        }
+        const bool nat = ex.g.C == 1;
+        TDH_TRY(prepare_typed<T>(st, ex, ex.g, nat ? st.u_nat : nullptr, nat ? half : 0, s));
+    }
+    return TDH_OK;
+}
+}  // namespace
+
+int exec_prepare_ragged(Step& st, int prec, cudaStream_t s) {
+    if (st.full || st.banded_M > 0) {
+        set_error("ragged batches are built for the parity-packed kinds");
+        return TDH_ERR_UNSUPPORTED;
+    }
+    if (prec == TDH_FP32) return prepare_ragged_typed<float>(st, prec, s);
+    return prepare_ragged_typed<double>(st, prec, s);
 }
 
 void exec_release(ExecData& ex) {
+    if (!ex.u_owned) ex.u = nullptr;
     dev_free(ex.perm);
     dev_free(ex.twl_hi);
     dev_free(ex.twl_lo);
@@ -397,6 +460,101 @@ void exec_release(ExecData& ex) {
     dev_free(ex.twp);
     dev_free(ex.u);
     ex = ExecData{};
+}
+
+namespace {
+
+// Group the vectors of a ragged batch by FFT length class (device side, any order).
+__global__ void k_classify(const int64_t* __restrict__ offs, int64_t batch, int64_t n_max,
+                           int ncls, int* __restrict__ count, int* __restrict__ list) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= batch) return;
+    const int64_t n = offs[i + 1] - offs[i];
+    if (n <= 0 || n > n_max) return;  // nothing to do / outside the plan (documented)
+    const int64_t m = (n + 1) / 2;
+    int logL = 8;
+    while (((int64_t)1 << logL) < 2 * m - 1) ++logL;
+    const int c = logL - 8;
+    if (c >= ncls) return;
+    const int idx = atomicAdd(&count[c], 1);
+    list[(int64_t)c * batch + idx] = (int)i;
+}
+
+template <typename T>
+int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t* offs,
+                        int64_t batch, cudaStream_t s, const std::vector<cudaStream_t>& side,
+                        const std::vector<cudaEvent_t>& ev) {
+    using V = typename cx<T>::t;
+    const int ncls = (int)st.rcls.size();
+    if ((int)side.size() < ncls || (int)ev.size() < ncls + 1) {
+        set_error("ragged execute: plan streams missing");
+        return TDH_ERR_INVALID_ARG;
+    }
+    int* scratch = nullptr;
+    const size_t words = 2 * (size_t)ncls + (size_t)ncls * batch;
+    TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(int) * words, s));
+    int* count = scratch;
+    int* next = scratch + ncls;
+    int* list = scratch + 2 * ncls;
+    int rc = TDH_OK;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * 2 * ncls, s);
+    if (e == cudaSuccess) {
+        k_classify<<<blocks_for(batch), kThreads, 0, s>>>(offs, batch, st.n, ncls, count, list);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    // longest class first; each class on its own stream
+    for (int c = ncls - 1; e == cudaSuccess && rc == TDH_OK && c >= 0; --c) {
+        const ExecData& ex = st.rcls[c];
+        cudaStream_t sc = side[c];
+        e = cudaStreamWaitEvent(sc, ev[0], 0);
+        if (e != cudaSuccess) break;
+        ExecParams<T> P;
+        P.in = static_cast<const T*>(in);
+        P.out = static_cast<T*>(out);
+        P.n = st.n;
+        P.K = st.K;
+        P.u = static_cast<const V*>(ex.u);
+        P.spec = static_cast<const V*>(ex.spec);
+        P.twx = static_cast<const V*>(ex.twx);
+        P.tw0 = static_cast<const V*>(ex.tw0);
+        P.twp = static_cast<const V*>(ex.twp);
+        P.din = static_cast<const T*>(st.d2x);
+        P.dout = static_cast<const T*>(st.d1x);
+        P.row0 = static_cast<const T*>(st.row0);
+        P.adjoint = 0;
+        P.full = 0;
+        P.sign_in = 0;
+        P.sign_out = 0;
+        P.u_stride = ex.u_stride;
+        P.ragged = 1;
+        P.offs = offs;
+        P.list = list + (int64_t)c * batch;
+        P.count = count + c;
+        P.next = next + c;
+        rc = dispatch<T>(ex.g, P, batch, sc);
+        if (rc == TDH_OK) e = cudaEventRecord(ev[1 + c], sc);
+        if (e == cudaSuccess && rc == TDH_OK) e = cudaStreamWaitEvent(s, ev[1 + c], 0);
+    }
+    if (e != cudaSuccess && rc == TDH_OK) {
+        set_error("ragged execute: %s", cudaGetErrorString(e));
+        rc = TDH_ERR_CUDA;
+    }
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (rc == TDH_OK && ef != cudaSuccess) {
+        set_error("cudaFreeAsync: %s", cudaGetErrorString(ef));
+        rc = TDH_ERR_CUDA;
+    }
+    return rc;
+}
+
+}  // namespace
+
+int exec_launch_ragged(const Step& st, int prec, const void* in, void* out, const int64_t* offs,
+                       int64_t batch, cudaStream_t s, const std::vector<cudaStream_t>& side,
+                       const std::vector<cudaEvent_t>& ev) {
+    if (prec == TDH_FP32) return launch_ragged_typed<float>(st, in, out, offs, batch, s, side, ev);
+    return launch_ragged_typed<double>(st, in, out, offs, batch, s, side, ev);
 }
 
 int exec_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,

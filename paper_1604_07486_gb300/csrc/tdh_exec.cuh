@@ -85,6 +85,14 @@ struct ExecParams {
     int full;       // 0: parity packing (x_2a, x_2a+1); 1: rank pairs (u_r, u_r+1) per index
     int sign_in;    // multiply input coefficient k by (-1)^k (Jacobi reflection)
     int sign_out;   // multiply output coefficient k by (-1)^k
+    int64_t u_stride;  // complex entries between consecutive (rank, k1) rows of u
+    // ragged batches: vector v occupies [offs[v], offs[v+1]); this launch converts the
+    // vectors list[0 .. *count) of one FFT-length class, taking them from the *next counter
+    int ragged;
+    const int64_t* offs;
+    const int* list;
+    const int* count;
+    int* next;
 };
 
 // XOR swizzle of shared-memory element indices: rows of 128 bytes, column ^= row.
@@ -167,34 +175,19 @@ __device__ __forceinline__ void middle_inv(V* buf, const V* twt) {
     }
 }
 
+// One vector: v = D alpha -> all K rank terms -> beta (the whole of Fig. 1 steps 3-5).
 template <typename T, int LOGLC, int R, int C, int NT>
-__global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
+__device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* in, T* out,
+                                               const int64_t n, const int k1,
+                                               typename cx<T>::t* buf, typename cx<T>::t* vbuf,
+                                               const typename cx<T>::t* twt, T* red) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
     constexpr int LC = G.LC();
     constexpr int S0 = LC / R;
     constexpr int J0 = S0 / NT;
     constexpr int RL = G.rad(G.np() - 1);  // radix of the last pass (stride 1)
-    constexpr int TWP = G.twp_len();
-    static_assert(G.np() >= 2, "local FFT needs at least two passes");
-    static_assert(J0 >= 1 && S0 % NT == 0, "pass-0 groups must divide over threads");
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* buf = reinterpret_cast<V*>(smem_raw);  // [LC], swizzled
-    V* vbuf = buf + LC;                       // [LC/2] scaled input pairs
-    V* twt = vbuf + LC / 2;                   // [TWP] middle-pass twiddles
-    __shared__ T red[NT / 32];
-
     const int tid = threadIdx.x;
-    int k1 = 0;
-    if constexpr (C > 1) k1 = (int)cg::this_cluster().block_rank();
-    const int64_t vec = blockIdx.x / C;
-    const int64_t n = P.n;
-    const T* in = P.in + vec * n;
-    T* out = P.out + vec * n;
-
-    for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
-    // v = D alpha in packed pairs; row-0 partial sum (Chebyshev-to-Legendre forward)
     T r0acc = T(0);
     for (int k2 = tid; k2 < LC / 2; k2 += NT) {
         const int64_t a = (int64_t)k1 + (int64_t)C * k2;
@@ -242,7 +235,7 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
 
 #pragma unroll 1
     for (int64_t r = 0; r < P.K; ++r) {
-        const V* ur = P.u + ((int64_t)r * C + k1) * (LC / 2);
+        const V* ur = P.u + ((int64_t)r * C + k1) * P.u_stride;
         // ---- forward pass 0: inputs u_r o v (upper half zero), radix R, stride S0
 #pragma unroll
         for (int j = 0; j < J0; ++j) {
@@ -407,6 +400,56 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
             if (tid == 0) out[0] = red[0];
         }
     }
+}
+
+template <typename T, int LOGLC, int R, int C, int NT>
+__global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
+    using V = typename cx<T>::t;
+    constexpr PassGeom G{LOGLC, R};
+    constexpr int LC = G.LC();
+    constexpr int S0 = LC / R;
+    constexpr int J0 = S0 / NT;
+    constexpr int TWP = G.twp_len();
+    static_assert(G.np() >= 2, "local FFT needs at least two passes");
+    static_assert(J0 >= 1 && S0 % NT == 0, "pass-0 groups must divide over threads");
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* buf = reinterpret_cast<V*>(smem_raw);  // [LC], swizzled
+    V* vbuf = buf + LC;                       // [LC/2] scaled input pairs
+    V* twt = vbuf + LC / 2;                   // [TWP] middle-pass twiddles
+    __shared__ T red[NT / 32];
+    __shared__ int slot[2];
+
+    const int tid = threadIdx.x;
+    int k1 = 0;
+    if constexpr (C > 1) k1 = (int)cg::this_cluster().block_rank();
+    for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
+    if (!P.ragged) {
+        const int64_t vec = blockIdx.x / C;
+        convert_vector<T, LOGLC, R, C, NT>(P, P.in + vec * P.n, P.out + vec * P.n, P.n, k1, buf,
+                                           vbuf, twt, red);
+        return;
+    }
+    // persistent: each cluster takes the next vector of its length class until none is left
+    const int count = *P.count;
+    for (int it = 0;; ++it) {
+        if (k1 == 0 && tid == 0) slot[it & 1] = atomicAdd(P.next, 1);
+        int sidx;
+        if constexpr (C > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            cl.sync();
+            sidx = *cl.map_shared_rank(&slot[it & 1], 0);
+        } else {
+            __syncthreads();
+            sidx = slot[it & 1];
+        }
+        if (sidx >= count) break;
+        const int64_t vec = P.list[sidx];
+        const int64_t off = P.offs[vec];
+        const int64_t n = P.offs[vec + 1] - off;
+        convert_vector<T, LOGLC, R, C, NT>(P, P.in + off, P.out + off, n, k1, buf, vbuf, twt, red);
+    }
+    if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its slot is read
 }
 
 }  // namespace tdh

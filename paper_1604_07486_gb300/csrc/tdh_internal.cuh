@@ -72,7 +72,9 @@ struct ExecData {
     void* tw0 = nullptr;  // [LC/R] complex: omega_LC^o, pass-0 twiddle bases
     void* twp = nullptr;  // later-pass twiddle tables, concatenated [p][o] blocks
     int64_t twp_len = 0;  // complex entries in twp
-    void* u = nullptr;    // [K][C][LC/2] complex: factors decimated by C (packed pairs)
+    void* u = nullptr;    // [K][C][u_stride] complex: factors decimated by C (packed pairs)
+    int64_t u_stride = 0;
+    bool u_owned = true;
     // multi-pass execution (C above the cluster limit: exchange through global memory)
     int multipass = 0;
     int* perm = nullptr;     // [LC] natural frequency of each local position
@@ -103,6 +105,9 @@ struct Step {
     void* d2x = nullptr;
     void* row0 = nullptr;  // CHEB2LEG: row 0 of A in execute precision, else null
     ExecData ex;
+    // ragged batches: one execute configuration per FFT length 2^(8+i), sharing u_nat
+    std::vector<ExecData> rcls;
+    void* u_nat = nullptr;  // [K][ceil(n/2)] packed factor pairs in execute precision
 };
 
 }  // namespace tdh
@@ -114,6 +119,8 @@ struct tdh_plan_s {
     double tol = 0;
     int device = 0;
     std::vector<tdh::Step> steps;
+    std::vector<cudaStream_t> side;  // ragged batches: one stream per length class
+    std::vector<cudaEvent_t> ev;     // fork/join events (ev[0] fork, ev[1+i] joins)
 };
 
 namespace tdh {
@@ -123,6 +130,12 @@ int banded_launch(int prec, const void* in, void* out, int64_t n, int64_t batch,
 // Build the execute configuration of `st` for precision `prec` (spectrum, twiddles, factors).
 int exec_prepare(Step& st, int prec, cudaStream_t s);
 void exec_release(ExecData& ex);
+// Configurations for every FFT length a ragged batch of vectors up to st.n can need.
+int exec_prepare_ragged(Step& st, int prec, cudaStream_t s);
+// Ragged batch: vector v = in[offs[v] .. offs[v+1]), length <= st.n.
+int exec_launch_ragged(const Step& st, int prec, const void* in, void* out, const int64_t* offs,
+                       int64_t batch, cudaStream_t s, const std::vector<cudaStream_t>& side,
+                       const std::vector<cudaEvent_t>& ev);
 // Multi-pass execute of one step (FFT longer than one cluster's shared memory).
 int mp_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
               cudaStream_t s);

@@ -1,0 +1,100 @@
+"""Ragged batches (vectors of different lengths in one call) against the oracle at each
+vector's own length: the n-prefix of an n_max plan converts the n-problem (needs a GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 5e-6}
+OKIND = {"leg2cheb": oracle.LEG2CHEB, "cheb2leg": oracle.CHEB2LEG}
+
+
+@pytest.fixture(scope="module")
+def tdh():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1604_07486_gb300 as m
+    from paper_1604_07486_gb300 import build
+    build.build()
+    return m
+
+
+def _check_vectors(y, x, offs, kind, idx, prec, max_dense=20000):
+    worst = 0.0
+    for i in idx:
+        a, b = int(offs[i]), int(offs[i + 1])
+        if b == a:
+            continue
+        n = b - a
+        rows = None if n <= max_dense else np.unique(np.r_[np.arange(48), n - 1 - np.arange(48),
+                                                            np.random.default_rng(i).integers(0, n, 64)])
+        ref = oracle.matvec(OKIND[kind], None, x[a:b], rows=rows)
+        got = y[a:b] if rows is None else y[a:b][rows]
+        worst = max(worst, np.abs(got - ref).max() / max(np.abs(x[a:b]).sum(), 1e-300))
+    assert worst <= TOL[prec], worst
+    return worst
+
+
+@pytest.mark.parametrize("kind", ["leg2cheb", "cheb2leg"])
+@pytest.mark.parametrize("prec,tol", [("fp32", None), ("fp64", None)])
+def test_ragged_small(tdh, kind, prec, tol):
+    """Lengths 0, 1, 2, ... up to 20000 (several FFT length classes, ragged tails)."""
+    import torch
+    if tol is None:
+        tol = {("leg2cheb", "fp64"): 1e-15, ("cheb2leg", "fp64"): 1e-17,
+               ("leg2cheb", "fp32"): 1e-7, ("cheb2leg", "fp32"): 1e-10}[(kind, prec)]
+    lengths = np.r_[[0, 1, 2, 3, 5, 128, 129, 257, 1000], workloads.ragged_degrees(40, 16, 20000, seed=3) + 1]
+    x, offs = workloads.ragged_coefficients(lengths, decay=1.0, seed=2)
+    plan = tdh.Plan(kind, int(lengths.max()), prec=prec, tol=tol, ragged=True)
+    xt = torch.tensor(x, dtype=plan.dtype, device="cuda")
+    ot = torch.tensor(offs, dtype=torch.int64, device="cuda")
+    y = plan.execute_ragged(xt, ot)
+    torch.cuda.synchronize()
+    _check_vectors(y.double().cpu().numpy(), x, offs, kind, range(len(lengths)), prec)
+
+
+def test_config3_ragged_4096(tdh):
+    """4096 Legendre -> Chebyshev vectors, degrees log-uniform in [64, 65536), alpha_k =
+    z_k/(k+1), float32: 24 vectors (the longest, the shortest and random ones) against the
+    oracle; the batch is also replayed from a captured CUDA graph with identical results."""
+    import torch
+    deg = workloads.ragged_degrees(4096, 64, 65536, seed=0)
+    lengths = deg + 1
+    x, offs = workloads.ragged_coefficients(lengths, decay=1.0, seed=0)
+    plan = tdh.Plan("leg2cheb", int(lengths.max()), prec="fp32", tol=1e-7, ragged=True)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    ot = torch.tensor(offs, dtype=torch.int64, device="cuda")
+    y = plan.execute_ragged(xt, ot)
+    torch.cuda.synchronize()
+    yn = y.double().cpu().numpy()
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.r_[np.argmax(lengths), np.argmin(lengths), rng.integers(0, 4096, 22)])
+    _check_vectors(yn, x, offs, "leg2cheb", idx, "fp32")
+    # CUDA graph: capture once, replay
+    out = torch.empty_like(xt)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.execute_ragged(xt, ot, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.execute_ragged(xt, ot, out=out)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, y)
+
+
+def test_ragged_requires_flag(tdh):
+    import torch
+    plan = tdh.Plan("leg2cheb", 100, prec="fp32")
+    x = torch.zeros(100, device="cuda")
+    offs = torch.tensor([0, 100], dtype=torch.int64, device="cuda")
+    with pytest.raises(tdh.TdhError) as e:
+        plan.execute_ragged(x, offs)
+    assert e.value.code == -1
