@@ -190,6 +190,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default): Leg<->Cheb n=2^16 batch 256; c1: Leg->Cheb n=1024 fp64; "
+                         "c3: ragged 4096 vectors; c4: Jacobi + ultraspherical n=2^20 batch 16; "
+                         "c5: autograd forward+backward n=8192 batch 1024")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -213,6 +217,11 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+    if args.workload != "c2":
+        run_extra(args, rank, world, local)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     def barrier():
         if world > 1:
@@ -364,6 +373,201 @@ def main():
     if world > 1:
         dist.destroy_process_group()
 
+
+
+def run_extra(args, rank, world, local):
+    """Configurations other than the default: one JSON line in the same schema."""
+    import math
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import paper_1604_07486_gb300 as tdh
+    from paper_1604_07486_gb300.autograd import convert
+    import workloads
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    hbm_peak = peaks.get("hbm_gbs", 6649.7)
+    w = args.workload
+    t0 = time.perf_counter()
+    extra = {}
+    if w == "c1":
+        n, B = 1024, 1
+        plan = tdh.Plan("leg2cheb", n, prec="fp64", tol=1e-15)
+        alpha = workloads.coefficients(n, B, decay=1.0, seed=rank)
+        x = torch.tensor(alpha, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        fn = lambda: plan.execute(x, out=y)
+        coeffs, dtype, launches = n * B, "f64", 1
+        flops = flops_per_vector(plan.K, 1024) * B
+        bound, peak, unit, pnote = "alu", 1.25, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s (GB300 table)"
+        config = {"workload": "leg2cheb n=1024 batch=1 fp64 tol=1e-15", "K": plan.K}
+        check = lambda: {"leg2cheb": float(np.abs(y.cpu().numpy() - oracle.matvec(oracle.LEG2CHEB, None, alpha)).max() / np.abs(alpha).sum())}
+        host_in = torch.from_numpy(alpha).pin_memory()
+        host_fn = lambda: plan.execute(host_in)
+        io = n * B * 8
+    elif w == "c3":
+        deg = workloads.ragged_degrees(4096, 64, 65536, seed=rank)
+        lengths = deg + 1
+        xv, offs = workloads.ragged_coefficients(lengths, decay=1.0, seed=rank)
+        plan = tdh.Plan("leg2cheb", int(lengths.max()), prec="fp32", tol=1e-7, ragged=True)
+        xt = torch.tensor(xv, dtype=torch.float32, device="cuda")
+        ot = torch.tensor(offs, dtype=torch.int64, device="cuda")
+        yt = torch.empty_like(xt)
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            plan.execute_ragged(xt, ot, out=yt)
+        stream.wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.execute_ragged(xt, ot, out=yt)
+        fn = graph.replay
+        coeffs, dtype = int(offs[-1]), "f32"
+        Ls = [max(256, 1 << int(math.ceil(math.log2(max(2 * ((int(n) + 1) // 2) - 1, 1))))) for n in lengths]
+        flops = sum(flops_per_vector(plan.K, L) for L in Ls)
+        launches = 1 + len([c for c in range(8, 17)])
+        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived"
+        config = {"workload": "ragged leg2cheb 4096 vectors, degrees log-uniform [64, 65536), fp32, one CUDA-graph launch",
+                  "K": plan.K, "coefficients": coeffs}
+        def check():
+            yn = yt.double().cpu().numpy()
+            errs = []
+            for i in [int(np.argmax(lengths)), 0, 1000, 4095]:
+                a, b = int(offs[i]), int(offs[i + 1])
+                rows = np.r_[np.arange(32), b - a - 32 + np.arange(32)]
+                ref = oracle.matvec(oracle.LEG2CHEB, None, xv[a:b], rows=rows)
+                errs.append(np.abs(yn[a:b][rows] - ref).max() / np.abs(xv[a:b]).sum())
+            return {"leg2cheb": float(max(errs))}
+        host_in = torch.from_numpy(xv.astype(np.float32)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        def host_fn():
+            xd = host_in.to("cuda", non_blocking=True)
+            od = ot
+            yd = plan.execute_ragged(xd, od)
+            host_out.copy_(yd, non_blocking=True)
+        io = coeffs * 4
+    elif w == "c4":
+        n, B = 1 << 20, 16
+        pj = tdh.Plan("jac2jac", n, prec="fp32", tol=1e-13, params=(0.1, -0.3, 0.0, 0.0))
+        pu = tdh.Plan("ultra2ultra", n, prec="fp32", tol=1e-13, params=(0.25, 1.25))
+        alpha = workloads.coefficients(n, B, decay=1.5, seed=rank)
+        x = torch.tensor(alpha, dtype=torch.float32, device="cuda")
+        yj, yu = torch.empty_like(x), torch.empty_like(x)
+        ev_mid = []
+        def fn():
+            pj.execute(x, out=yj)
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            ev_mid.append(e)
+            pu.execute(x, out=yu)
+        coeffs, dtype = 2 * n * B, "f32"
+        # both Jacobi steps: rank pairs packed, FFT length 2^21 (factor count from the plan)
+        flops = 2 * flops_per_vector(pj.K, 1 << 21) / 2 * B
+        launches = None
+        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived (Jacobi multi-pass part)"
+        config = {"workload": "jacobi (0.1,-0.3)->(0,0) + ultraspherical 0.25->1.25, n=2^20, batch=16, fp32 execute, fp64 plan, tol 1e-13",
+                  "K_jacobi_max_step": pj.K}
+        check = None
+        host_in = torch.from_numpy(alpha.astype(np.float32)).pin_memory()
+        def host_fn():
+            pj.execute(host_in)
+            pu.execute(host_in)
+        io = 2 * n * B * 4
+    elif w == "c5":
+        n, B = 8192, 1024
+        plan = tdh.Plan("leg2cheb", n, prec="fp32", tol=1e-7)
+        alpha = workloads.coefficients(n, B, decay=1.0, seed=rank)
+        x = torch.tensor(alpha, dtype=torch.float32, device="cuda", requires_grad=True)
+        wgt = (torch.arange(n, device="cuda", dtype=torch.float32) + 1.0) ** 2
+        def fn():
+            x.grad = None
+            beta = convert(x, plan)
+            (wgt * beta * beta).sum().backward()
+        coeffs, dtype = n * B, "f32"
+        flops = 2 * flops_per_vector(plan.K, 8192) * B
+        launches = 2
+        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived"
+        config = {"workload": "autograd leg2cheb n=8192 batch=1024 fp32: forward + loss + backward (adjoint kernel)", "K": plan.K}
+        def check():
+            fn()
+            g = x.grad.double().cpu().numpy()
+            beta = plan.execute(x.detach()).double().cpu().numpy()
+            cot = 2.0 * (np.arange(n) + 1.0) ** 2 * beta
+            ref = oracle.matvec(oracle.LEG2CHEB, None, cot[[0, B - 1]], transpose=True)
+            return {"grad": float((np.abs(g[[0, B - 1]] - ref).max(axis=1) / np.abs(cot[[0, B - 1]]).sum(axis=1)).max())}
+        host_in = torch.from_numpy(alpha.astype(np.float32)).pin_memory()
+        host_fn = lambda: plan.execute(host_in)
+        io = n * B * 4
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    with sampler:
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            fn()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * coeffs * args.steps / (total_ms / 1e3)
+    achieved = flops * args.steps / (total_ms / 1e3) / 1e12
+    if w == "c4" and ev_mid:
+        # split: Jacobi part vs ultraspherical (sparse factor, HBM-bound) part
+        jac_ms = [evs[i][0].elapsed_time(ev_mid[-args.steps + i]) for i in range(args.steps)]
+        ult_ms = [ev_mid[-args.steps + i].elapsed_time(evs[i][1]) for i in range(args.steps)]
+        achieved = flops * args.steps / (sum(jac_ms) / 1e3) / 1e12
+        band_gbs = 8.0 * n * B * args.steps / (sum(ult_ms) / 1e3) / 1e9
+        extra["split_ms"] = {"jacobi": statistics.mean(jac_ms), "ultraspherical": statistics.mean(ult_ms)}
+        extra["banded_roofline"] = {"bound": "hbm", "achieved": band_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                    "frac": band_gbs / hbm_peak, "traffic": None,
+                                    "note": "8 algorithmic bytes per coefficient; of measured"}
+    err = check() if (check and rank == 0) else None
+    # end to end through the public API with pinned host buffers
+    for _ in range(2):
+        host_fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = 3
+    for _ in range(reps):
+        host_fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = world * coeffs * reps / (e0.elapsed_time(e1) / 1e3)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "coeffs/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+                "data": "synthetic", "config": dict(config, plan_ms=plan_ms,
+                                                    l2="flushed between steps (256 MB write)"),
+                "error_vs_oracle": err,
+                "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                             "frac": achieved / peak, "traffic": None, "peak_note": pnote},
+                "e2e": {"value": e2e, "unit": "coeffs/s", "h2d_bytes_per_step": io, "d2h_bytes_per_step": io},
+                "gpu_launches": launches * args.steps if launches else None,
+                "clocks": sampler.summary(), "cpu_baseline": None}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
 
 if __name__ == "__main__":
     main()

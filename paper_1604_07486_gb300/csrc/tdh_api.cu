@@ -52,6 +52,7 @@ void release_step(Step& st) {
     for (auto& ex : st.rcls) exec_release(ex);
     st.rcls.clear();
     dev_free(st.u_nat);
+    dev_free(st.band_coef);
     dev_free(st.t);
     dev_free(st.h);
     dev_free(st.d1);
@@ -68,7 +69,8 @@ void release_step(Step& st) {
 // Build one conversion step: symbols (a1), pivoted Cholesky (a2), execute tables (a3).
 int build_step(Step& st, double tol, int64_t kmax, int prec, cudaStream_t s) {
     const int64_t n = st.n;
-    if (st.banded_M > 0) return TDH_OK;  // sparse factors need no plan data
+    if (st.banded_M > 0)  // sparse factors: only their coefficient table
+        return banded_prepare(prec, n, st.banded_lam0, st.banded_M, &st.band_coef, s);
     TDH_TRY(dev_alloc_t(&st.t, n));
     TDH_TRY(dev_alloc_t(&st.h, 2 * n - 1));
     TDH_TRY(dev_alloc_t(&st.d1, n));
@@ -151,7 +153,7 @@ int run(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream,
                           "(not built)");
                 return TDH_ERR_UNSUPPORTED;
             }
-            TDH_TRY(banded_launch(plan->params.prec, in, out, st.n, batch, st.banded_lam0,
+            TDH_TRY(banded_launch(plan->params.prec, in, out, st.n, batch, st.band_coef,
                                   st.banded_M, adjoint, s));
             continue;
         }

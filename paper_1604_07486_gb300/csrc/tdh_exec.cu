@@ -278,89 +278,9 @@ int prepare_diagonals(Step& st, cudaStream_t s) {
 
 // ----------------------------------------------------------------------------- launch
 
-template <typename T, int LOGLC, int R, int C, int NT>
-int launch_inst(const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
-    using V = typename cx<T>::t;
-    constexpr PassGeom G{LOGLC, R};
-    constexpr size_t smem = (size_t)(G.LC() + G.LC() / 2 + G.twp_len()) * sizeof(V);
-    static_assert(smem <= 232448, "shared memory budget");
-    auto kern = exec_kernel<T, LOGLC, R, C, NT>;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    });
-    if (attr_err != cudaSuccess) {
-        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(attr_err));
-        return TDH_ERR_CUDA;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(batch * C), 1, 1);
-    cfg.blockDim = dim3(NT, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    if (C > 1) {
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-    }
-    if (P.ragged) {
-        // persistent: as many clusters as can be resident, at most one per vector
-        int resident = 0;
-        if (C > 1) {
-            TDH_CUDA(cudaOccupancyMaxActiveClusters(&resident, kern, &cfg));
-        } else {
-            int per_sm = 0;
-            TDH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-            resident = per_sm * sm_count();
-        }
-        const int64_t nclusters = std::max<int64_t>(1, std::min<int64_t>(batch, resident));
-        cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
-    }
-    TDH_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
-    return TDH_OK;
-}
-
 template <typename T>
-int dispatch(const Geometry& g, const ExecParams<T>& P, int64_t batch, cudaStream_t s);
-
-template <>
-int dispatch<float>(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s) {
-    switch (g.logLC * 16 + g.C) {
-    case 8 * 16 + 1: return launch_inst<float, 8, 8, 1, 32>(P, batch, s);
-    case 9 * 16 + 1: return launch_inst<float, 9, 8, 1, 64>(P, batch, s);
-    case 10 * 16 + 1: return launch_inst<float, 10, 16, 1, 64>(P, batch, s);
-    case 11 * 16 + 1: return launch_inst<float, 11, 16, 1, 128>(P, batch, s);
-    case 12 * 16 + 1: return launch_inst<float, 12, 16, 1, 256>(P, batch, s);
-    case 13 * 16 + 1: return launch_inst<float, 13, 16, 1, 512>(P, batch, s);
-    case 14 * 16 + 1: return launch_inst<float, 14, 16, 1, 512>(P, batch, s);
-    case 14 * 16 + 2: return launch_inst<float, 14, 16, 2, 512>(P, batch, s);
-    case 14 * 16 + 4: return launch_inst<float, 14, 16, 4, 512>(P, batch, s);
-    case 14 * 16 + 8: return launch_inst<float, 14, 16, 8, 512>(P, batch, s);
-    }
-    set_error("no float32 kernel for local length 2^%d, cluster %d", g.logLC, g.C);
-    return TDH_ERR_UNSUPPORTED;
-}
-
-template <>
-int dispatch<double>(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s) {
-    switch (g.logLC * 16 + g.C) {
-    case 8 * 16 + 1: return launch_inst<double, 8, 8, 1, 32>(P, batch, s);
-    case 9 * 16 + 1: return launch_inst<double, 9, 8, 1, 64>(P, batch, s);
-    case 10 * 16 + 1: return launch_inst<double, 10, 8, 1, 128>(P, batch, s);
-    case 11 * 16 + 1: return launch_inst<double, 11, 8, 1, 256>(P, batch, s);
-    case 12 * 16 + 1: return launch_inst<double, 12, 8, 1, 512>(P, batch, s);
-    case 13 * 16 + 1: return launch_inst<double, 13, 8, 1, 512>(P, batch, s);
-    case 13 * 16 + 2: return launch_inst<double, 13, 8, 2, 512>(P, batch, s);
-    case 13 * 16 + 4: return launch_inst<double, 13, 8, 4, 512>(P, batch, s);
-    case 13 * 16 + 8: return launch_inst<double, 13, 8, 8, 512>(P, batch, s);
-    }
-    set_error("no float64 kernel for local length 2^%d, cluster %d", g.logLC, g.C);
-    return TDH_ERR_UNSUPPORTED;
+int dispatch(const Geometry& g, const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
+    return P.ragged ? dispatch_ragged(g, P, batch, s) : dispatch_dense(g, P, batch, s);
 }
 
 template <typename T>
@@ -562,6 +482,13 @@ int exec_launch(const Step& st, int prec, const void* in, void* out, int64_t bat
     if (st.ex.multipass) return mp_launch(st, prec, in, out, batch, adjoint, s);
     if (prec == TDH_FP32) return launch_typed<float>(st, in, out, batch, adjoint, s);
     return launch_typed<double>(st, in, out, batch, adjoint, s);
+}
+
+int dispatch_dense(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s) {
+    return dispatch_geom<float, false>(g, P, batch, s);
+}
+int dispatch_dense(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s) {
+    return dispatch_geom<double, false>(g, P, batch, s);
 }
 
 }  // namespace tdh

@@ -21,6 +21,10 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <mutex>
+#include <type_traits>
+
 #include "tdh_fft.cuh"
 #include "tdh_internal.cuh"
 
@@ -95,11 +99,60 @@ struct ExecParams {
     int* next;
 };
 
-// XOR swizzle of shared-memory element indices: rows of 128 bytes, column ^= row.
+#ifndef TDH_SMEM_PAD
+#define TDH_SMEM_PAD 0
+#endif
+#if TDH_SMEM_PAD
+// Shared-memory index of FFT element i: one padding element after every 128-byte row.
 template <typename V>
-__device__ __forceinline__ int swz(int i) {
+__device__ __forceinline__ int sidx(int i) {
+    constexpr int epr = 128 / (int)sizeof(V);
+    return i + i / epr;
+}
+template <typename V>
+__host__ __device__ constexpr int padded_len(int n) {
+    return n + n / (128 / (int)sizeof(V));
+}
+// element pair (2k, 2k+1) -> (first address, swapped?)
+template <typename V>
+__device__ __forceinline__ bool pair_swapped(int) { return false; }
+#else
+// Shared-memory index of FFT element i: XOR swizzle within 128-byte rows (column ^= row),
+// free of bank conflicts for every pass's access pattern.
+template <typename V>
+__device__ __forceinline__ int sidx(int i) {
     constexpr int epr = 128 / (int)sizeof(V);
     return i ^ ((i / epr) & (epr - 1));
+}
+template <typename V>
+__host__ __device__ constexpr int padded_len(int n) {
+    return n;
+}
+// The aligned pair (2k, 2k+1) stays an aligned pair under the swizzle, swapped when bit 0 of
+// its row index is set.
+template <typename V>
+__device__ __forceinline__ bool pair_swapped(int i) {
+    constexpr int epr = 128 / (int)sizeof(V);
+    return ((i / epr) & 1) != 0;
+}
+#endif
+
+// Two consecutive complex values as one 16-byte (float) or two 16-byte (double) accesses.
+__device__ __forceinline__ void pair_load(const float2* p, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void pair_store(float2* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void pair_load(const double2* p, double2& a, double2& b) {
+    a = p[0];
+    b = p[1];
+}
+__device__ __forceinline__ void pair_store(double2* p, double2 a, double2 b) {
+    p[0] = a;
+    p[1] = b;
 }
 
 // powers w^p, p in [0, R), from w^1 by a binary tree of products (error ~ log2(p) ulp)
@@ -116,28 +169,35 @@ __device__ __forceinline__ void powers(V w1, V (&wp)[R]) {
 }
 
 // Middle forward pass i: radix RAD, sub-length M, stride S, twiddles from the [p][o] table.
+// Every group g = tid + i NT of a thread has the same offset o = g % S (NT is a multiple of
+// S), so its twiddles omega_M^{p o} are powers of one table entry, formed once per pass in
+// registers instead of read per group from shared memory.
 template <int RAD, int M, int S, int LC, int NT, typename V>
 __device__ __forceinline__ void pass_fwd(V* buf, const V* tw) {
+    static_assert(NT % S == 0, "thread count must be a multiple of the pass stride");
+    V wp[RAD];
+    powers<RAD>(tw[S + (int)threadIdx.x % S], wp);
 #pragma unroll 1
     for (int g = threadIdx.x; g < LC / RAD; g += NT) {
         const int b = g / S, o = g % S;
         const int base = b * M + o;
         V x[RAD];
 #pragma unroll
-        for (int q = 0; q < RAD; ++q) x[q] = buf[swz<V>(base + q * S)];
+        for (int q = 0; q < RAD; ++q) x[q] = buf[sidx<V>(base + q * S)];
         dif<RAD>(x);
 #pragma unroll
         for (int jj = 0; jj < RAD; ++jj) {
             const int p = bitrev(jj, RAD);
-            V y = x[jj];
-            if (p != 0) y = cmul(y, tw[p * S + o]);
-            buf[swz<V>(base + p * S)] = y;
+            buf[sidx<V>(base + p * S)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
         }
     }
 }
 
 template <int RAD, int M, int S, int LC, int NT, typename V>
 __device__ __forceinline__ void pass_inv(V* buf, const V* tw) {
+    static_assert(NT % S == 0, "thread count must be a multiple of the pass stride");
+    V wp[RAD];
+    powers<RAD>(tw[S + (int)threadIdx.x % S], wp);
 #pragma unroll 1
     for (int g = threadIdx.x; g < LC / RAD; g += NT) {
         const int b = g / S, o = g % S;
@@ -145,13 +205,12 @@ __device__ __forceinline__ void pass_inv(V* buf, const V* tw) {
         V x[RAD];
 #pragma unroll
         for (int p = 0; p < RAD; ++p) {
-            V y = buf[swz<V>(base + p * S)];
-            if (p != 0) y = cmulc(y, tw[p * S + o]);
-            x[bitrev(p, RAD)] = y;
+            const V y = buf[sidx<V>(base + p * S)];
+            x[bitrev(p, RAD)] = (p == 0) ? y : cmulc(y, wp[p]);
         }
         dit<RAD>(x);
 #pragma unroll
-        for (int q = 0; q < RAD; ++q) buf[swz<V>(base + q * S)] = x[q];
+        for (int q = 0; q < RAD; ++q) buf[sidx<V>(base + q * S)] = x[q];
     }
 }
 
@@ -249,7 +308,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 #pragma unroll
             for (int jj = 0; jj < R; ++jj) {
                 const int p = bitrev(jj, R);
-                buf[swz<V>(o + p * S0)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
+                buf[sidx<V>(o + p * S0)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
             }
         }
         __syncthreads();
@@ -260,7 +319,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             for (int g = tid; g < LC / RL; g += NT) {
                 V x[RL];
 #pragma unroll
-                for (int q = 0; q < RL; ++q) x[q] = buf[swz<V>(g * RL + q)];
+                for (int q = 0; q < RL; ++q) x[q] = buf[sidx<V>(g * RL + q)];
                 dif<RL>(x);
 #pragma unroll
                 for (int jj = 0; jj < RL; ++jj) {
@@ -269,51 +328,81 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
                 }
                 dit<RL>(x);
 #pragma unroll
-                for (int q = 0; q < RL; ++q) buf[swz<V>(g * RL + q)] = x[q];
+                for (int q = 0; q < RL; ++q) buf[sidx<V>(g * RL + q)] = x[q];
             }
             __syncthreads();
         } else {
+            // Last local pass (radix RL, stride 1), then the cross-CTA stage, then the first
+            // inverse local pass.  In the cross stage each thread takes two consecutive
+            // positions, so every access to another CTA's shared memory moves 16 bytes.
+            // CTA k1 owns positions [k1 LC/C, (k1+1) LC/C).
+            constexpr int PPC = LC / C;
+            static_assert(PPC % (2 * NT) == 0, "two positions per thread");
             cg::cluster_group cl = cg::this_cluster();
 #pragma unroll 1
             for (int g = tid; g < LC / RL; g += NT) {
                 V x[RL];
 #pragma unroll
-                for (int q = 0; q < RL; ++q) x[q] = buf[swz<V>(g * RL + q)];
+                for (int q = 0; q < RL; ++q) x[q] = buf[sidx<V>(g * RL + q)];
                 dif<RL>(x);
 #pragma unroll
-                for (int jj = 0; jj < RL; ++jj) buf[swz<V>(g * RL + bitrev(jj, RL))] = x[jj];
+                for (int jj = 0; jj < RL; ++jj) buf[sidx<V>(g * RL + bitrev(jj, RL))] = x[jj];
             }
             cl.sync();
-            // cross-CTA stage for positions owned by this CTA
 #pragma unroll 1
-            for (int pos = k1 * (LC / C) + tid; pos < (k1 + 1) * (LC / C); pos += NT) {
-                const int sp = swz<V>(pos);
-                const V tw = P.twx[pos];
-                V a[C], twj[C];
-                twj[0] = mk<V>(1, 0);
+            for (int pi = 2 * tid; pi < PPC; pi += 2 * NT) {
+                const int pos = k1 * PPC + pi;  // even: the pair (pos, pos+1) is contiguous
+                const bool swp = pair_swapped<V>(pos);
+                const int sp = sidx<V>(pos) & ~1;
+                V a[2][C], sc[2][C], tw[2];
 #pragma unroll
-                for (int j = 1; j < C; ++j) twj[j] = cmul(twj[j - 1], tw);
-#pragma unroll
-                for (int j = 0; j < C; ++j) a[j] = cmul(rbuf[j][sp], twj[j]);
-                dif<C>(a);
-#pragma unroll
-                for (int jj = 0; jj < C; ++jj) {
-                    const V s = P.spec[(int64_t)pos * C + bitrev(jj, C)];
-                    a[jj] = P.adjoint ? cmulc(a[jj], s) : cmul(a[jj], s);
+                for (int j = 0; j < C; ++j) {
+                    V e0, e1;
+                    pair_load(rbuf[j] + sp, e0, e1);
+                    a[0][j] = swp ? e1 : e0;
+                    a[1][j] = swp ? e0 : e1;
                 }
-                dit<C>(a);
+                pair_load(P.twx + pos, tw[0], tw[1]);
 #pragma unroll
-                for (int j = 0; j < C; ++j) rbuf[j][sp] = cmulc(a[j], twj[j]);
+                for (int f = 0; f < C; f += 2) {
+                    pair_load(P.spec + (int64_t)pos * C + f, sc[0][f], sc[0][f + 1]);
+                    pair_load(P.spec + (int64_t)(pos + 1) * C + f, sc[1][f], sc[1][f + 1]);
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    V twj[C];
+                    twj[0] = mk<V>(1, 0);
+#pragma unroll
+                    for (int j = 1; j < C; ++j) twj[j] = cmul(twj[j - 1], tw[u]);
+#pragma unroll
+                    for (int j = 0; j < C; ++j) a[u][j] = cmul(a[u][j], twj[j]);
+                    dif<C>(a[u]);
+#pragma unroll
+                    for (int ff = 0; ff < C; ++ff) {
+                        const V sv = sc[u][bitrev(ff, C)];
+                        a[u][ff] = P.adjoint ? cmulc(a[u][ff], sv) : cmul(a[u][ff], sv);
+                    }
+                    dit<C>(a[u]);
+#pragma unroll
+                    for (int j = 0; j < C; ++j) a[u][j] = cmulc(a[u][j], twj[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < C; ++j) {
+                    if (swp)
+                        pair_store(rbuf[j] + sp, a[1][j], a[0][j]);
+                    else
+                        pair_store(rbuf[j] + sp, a[0][j], a[1][j]);
+                }
             }
             cl.sync();
 #pragma unroll 1
             for (int g = tid; g < LC / RL; g += NT) {
                 V x[RL];
 #pragma unroll
-                for (int p = 0; p < RL; ++p) x[bitrev(p, RL)] = buf[swz<V>(g * RL + p)];
+                for (int p = 0; p < RL; ++p) x[bitrev(p, RL)] = buf[sidx<V>(g * RL + p)];
                 dit<RL>(x);
 #pragma unroll
-                for (int q = 0; q < RL; ++q) buf[swz<V>(g * RL + q)] = x[q];
+                for (int q = 0; q < RL; ++q) buf[sidx<V>(g * RL + q)] = x[q];
             }
             __syncthreads();
         }
@@ -327,7 +416,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             V x[R];
 #pragma unroll
             for (int p = 0; p < R; ++p) {
-                const V y = buf[swz<V>(o + p * S0)];
+                const V y = buf[sidx<V>(o + p * S0)];
                 x[bitrev(p, R)] = (p == 0) ? y : cmulc(y, wp[p]);
             }
             dit_halfout<R>(x);
@@ -402,7 +491,10 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
     }
 }
 
-template <typename T, int LOGLC, int R, int C, int NT>
+// Dense batches: cluster blockIdx.x / C converts vector blockIdx.x / C.  Ragged batches
+// (RAGGED): persistent clusters take vectors of one FFT-length class from a work counter.
+// Two kernels so that each inlines the per-vector body once (register pressure).
+template <typename T, int LOGLC, int R, int C, int NT, bool RAGGED>
 __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
@@ -414,42 +506,129 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
     static_assert(J0 >= 1 && S0 % NT == 0, "pass-0 groups must divide over threads");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* buf = reinterpret_cast<V*>(smem_raw);  // [LC], swizzled
-    V* vbuf = buf + LC;                       // [LC/2] scaled input pairs
+    V* buf = reinterpret_cast<V*>(smem_raw);  // [LC] FFT buffer, padded rows
+    V* vbuf = buf + padded_len<V>(LC);        // [LC/2] scaled input pairs
     V* twt = vbuf + LC / 2;                   // [TWP] middle-pass twiddles
     __shared__ T red[NT / 32];
-    __shared__ int slot[2];
 
     const int tid = threadIdx.x;
     int k1 = 0;
     if constexpr (C > 1) k1 = (int)cg::this_cluster().block_rank();
     for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
-    if (!P.ragged) {
+    if constexpr (!RAGGED) {
         const int64_t vec = blockIdx.x / C;
         convert_vector<T, LOGLC, R, C, NT>(P, P.in + vec * P.n, P.out + vec * P.n, P.n, k1, buf,
                                            vbuf, twt, red);
-        return;
-    }
-    // persistent: each cluster takes the next vector of its length class until none is left
-    const int count = *P.count;
-    for (int it = 0;; ++it) {
-        if (k1 == 0 && tid == 0) slot[it & 1] = atomicAdd(P.next, 1);
-        int sidx;
-        if constexpr (C > 1) {
-            cg::cluster_group cl = cg::this_cluster();
-            cl.sync();
-            sidx = *cl.map_shared_rank(&slot[it & 1], 0);
-        } else {
-            __syncthreads();
-            sidx = slot[it & 1];
+    } else {
+        __shared__ int slot[2];
+        const int count = *P.count;
+        for (int it = 0;; ++it) {
+            if (k1 == 0 && tid == 0) slot[it & 1] = atomicAdd(P.next, 1);
+            int sidx;
+            if constexpr (C > 1) {
+                cg::cluster_group cl = cg::this_cluster();
+                cl.sync();
+                sidx = *cl.map_shared_rank(&slot[it & 1], 0);
+            } else {
+                __syncthreads();
+                sidx = slot[it & 1];
+            }
+            if (sidx >= count) break;
+            const int64_t vec = P.list[sidx];
+            const int64_t off = P.offs[vec];
+            const int64_t n = P.offs[vec + 1] - off;
+            convert_vector<T, LOGLC, R, C, NT>(P, P.in + off, P.out + off, n, k1, buf, vbuf, twt,
+                                               red);
         }
-        if (sidx >= count) break;
-        const int64_t vec = P.list[sidx];
-        const int64_t off = P.offs[vec];
-        const int64_t n = P.offs[vec + 1] - off;
-        convert_vector<T, LOGLC, R, C, NT>(P, P.in + off, P.out + off, n, k1, buf, vbuf, twt, red);
+        if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its slot is read
     }
-    if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its slot is read
 }
+
+template <typename T, int LOGLC, int R, int C, int NT, bool RAGGED>
+int launch_inst(const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
+    using V = typename cx<T>::t;
+    constexpr PassGeom G{LOGLC, R};
+    constexpr size_t smem = (size_t)(padded_len<V>(G.LC()) + G.LC() / 2 + G.twp_len()) * sizeof(V);
+    static_assert(smem <= 232448, "shared memory budget");
+    auto kern = exec_kernel<T, LOGLC, R, C, NT, RAGGED>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) {
+        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(attr_err));
+        return TDH_ERR_CUDA;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(batch * C), 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (C > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    if constexpr (RAGGED) {
+        // persistent: as many clusters as can be resident, at most one per vector
+        int resident = 0;
+        if (C > 1) {
+            TDH_CUDA(cudaOccupancyMaxActiveClusters(&resident, kern, &cfg));
+        } else {
+            int per_sm = 0;
+            TDH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+            resident = per_sm * sm_count();
+        }
+        const int64_t nclusters = std::max<int64_t>(1, std::min<int64_t>(batch, resident));
+        cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
+    }
+    TDH_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
+    return TDH_OK;
+}
+
+// Kernel instantiation for a geometry (switch over the built configurations).
+template <typename T, bool RAGGED>
+int dispatch_geom(const Geometry& g, const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        switch (g.logLC * 16 + g.C) {
+        case 8 * 16 + 1: return launch_inst<float, 8, 8, 1, 32, RAGGED>(P, batch, s);
+        case 9 * 16 + 1: return launch_inst<float, 9, 8, 1, 64, RAGGED>(P, batch, s);
+        case 10 * 16 + 1: return launch_inst<float, 10, 16, 1, 64, RAGGED>(P, batch, s);
+        case 11 * 16 + 1: return launch_inst<float, 11, 16, 1, 128, RAGGED>(P, batch, s);
+        case 12 * 16 + 1: return launch_inst<float, 12, 16, 1, 256, RAGGED>(P, batch, s);
+        case 13 * 16 + 1: return launch_inst<float, 13, 16, 1, 512, RAGGED>(P, batch, s);
+        case 14 * 16 + 1: return launch_inst<float, 14, 16, 1, 512, RAGGED>(P, batch, s);
+        case 14 * 16 + 2: return launch_inst<float, 14, 16, 2, 512, RAGGED>(P, batch, s);
+        case 14 * 16 + 4: return launch_inst<float, 14, 16, 4, 512, RAGGED>(P, batch, s);
+        case 14 * 16 + 8: return launch_inst<float, 14, 16, 8, 512, RAGGED>(P, batch, s);
+        }
+    } else {
+        switch (g.logLC * 16 + g.C) {
+        case 8 * 16 + 1: return launch_inst<double, 8, 8, 1, 32, RAGGED>(P, batch, s);
+        case 9 * 16 + 1: return launch_inst<double, 9, 8, 1, 64, RAGGED>(P, batch, s);
+        case 10 * 16 + 1: return launch_inst<double, 10, 8, 1, 128, RAGGED>(P, batch, s);
+        case 11 * 16 + 1: return launch_inst<double, 11, 8, 1, 256, RAGGED>(P, batch, s);
+        case 12 * 16 + 1: return launch_inst<double, 12, 8, 1, 512, RAGGED>(P, batch, s);
+        case 13 * 16 + 1: return launch_inst<double, 13, 8, 1, 512, RAGGED>(P, batch, s);
+        case 13 * 16 + 2: return launch_inst<double, 13, 8, 2, 512, RAGGED>(P, batch, s);
+        case 13 * 16 + 4: return launch_inst<double, 13, 8, 4, 512, RAGGED>(P, batch, s);
+        case 13 * 16 + 8: return launch_inst<double, 13, 8, 8, 512, RAGGED>(P, batch, s);
+        }
+    }
+    set_error("no %s kernel for local length 2^%d, cluster %d",
+              std::is_same<T, float>::value ? "float32" : "float64", g.logLC, g.C);
+    return TDH_ERR_UNSUPPORTED;
+}
+
+// Defined in tdh_exec.cu (dense) and tdh_ragged.cu (ragged), one instantiation set each.
+int dispatch_dense(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s);
+int dispatch_dense(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s);
+int dispatch_ragged(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s);
+int dispatch_ragged(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s);
 
 }  // namespace tdh

@@ -95,6 +95,7 @@ struct Step {
     int sign_out = 0;      // (-1)^k on the output
     int banded_M = 0;      // > 0: Case-1 step of M sparse factors S_l, no T o H (Sec. 5.2)
     double banded_lam0 = 0;  // first factor's l
+    void* band_coef = nullptr;  // [M][n+2] l/(l+j) in execute precision
     double* t = nullptr;   // [n]
     double* h = nullptr;   // [2n-1]
     double* d1 = nullptr;  // [n]
@@ -124,8 +125,10 @@ struct tdh_plan_s {
 };
 
 namespace tdh {
-// Case-1 sparse factors: out = S_{l0+M-1} ... S_{l0} in (or the transpose); out != in.
-int banded_launch(int prec, const void* in, void* out, int64_t n, int64_t batch, double lam0,
+// Case-1 sparse factors: coefficient tables, then out = S_{l0+M-1} ... S_{l0} in (or the
+// transpose); out != in.
+int banded_prepare(int prec, int64_t n, double lam0, int M, void** coef, cudaStream_t s);
+int banded_launch(int prec, const void* in, void* out, int64_t n, int64_t batch, const void* coef,
                   int M, int adjoint, cudaStream_t s);
 // Build the execute configuration of `st` for precision `prec` (spectrum, twiddles, factors).
 int exec_prepare(Step& st, int prec, cudaStream_t s);

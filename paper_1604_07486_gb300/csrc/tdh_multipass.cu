@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NT, 1) mp_fwd(const MPParams<T> P, int64_t r) 
     constexpr int TWP = G.twp_len();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* buf = reinterpret_cast<V*>(smem_raw);
-    V* twt = buf + LC;
+    V* twt = buf + padded_len<V>(LC);
     const int tid = threadIdx.x;
     const int64_t bl = blockIdx.x / P.C;
     const int k1 = blockIdx.x % P.C;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(NT, 1) mp_fwd(const MPParams<T> P, int64_t r) 
 #pragma unroll
         for (int jj = 0; jj < R; ++jj) {
             const int p = bitrev(jj, R);
-            buf[swz<V>(o + p * S0)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
+            buf[sidx<V>(o + p * S0)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
         }
     }
     __syncthreads();
@@ -144,14 +144,14 @@ __global__ void __launch_bounds__(NT, 1) mp_fwd(const MPParams<T> P, int64_t r) 
     for (int g = tid; g < LC / RL; g += NT) {
         V x[RL];
 #pragma unroll
-        for (int q = 0; q < RL; ++q) x[q] = buf[swz<V>(g * RL + q)];
+        for (int q = 0; q < RL; ++q) x[q] = buf[sidx<V>(g * RL + q)];
         dif<RL>(x);
 #pragma unroll
-        for (int jj = 0; jj < RL; ++jj) buf[swz<V>(g * RL + bitrev(jj, RL))] = x[jj];
+        for (int jj = 0; jj < RL; ++jj) buf[sidx<V>(g * RL + bitrev(jj, RL))] = x[jj];
     }
     __syncthreads();
     V* y = P.Y + (bl * P.C + k1) * LC;
-    for (int pos = tid; pos < LC; pos += NT) y[pos] = buf[swz<V>(pos)];
+    for (int pos = tid; pos < LC; pos += NT) y[pos] = buf[sidx<V>(pos)];
 }
 
 template <typename T, int LOGLC, int R, int NT>
@@ -162,22 +162,22 @@ __global__ void __launch_bounds__(NT, 1) mp_inv(const MPParams<T> P, int64_t r) 
     constexpr int TWP = G.twp_len();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* buf = reinterpret_cast<V*>(smem_raw);
-    V* twt = buf + LC;
+    V* twt = buf + padded_len<V>(LC);
     const int tid = threadIdx.x;
     const int64_t bl = blockIdx.x / P.C;
     const int k1 = blockIdx.x % P.C;
     for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
     const V* y = P.Y + (bl * P.C + k1) * LC;
-    for (int pos = tid; pos < LC; pos += NT) buf[swz<V>(pos)] = y[pos];
+    for (int pos = tid; pos < LC; pos += NT) buf[sidx<V>(pos)] = y[pos];
     __syncthreads();
 #pragma unroll 1
     for (int g = tid; g < LC / RL; g += NT) {
         V x[RL];
 #pragma unroll
-        for (int p = 0; p < RL; ++p) x[bitrev(p, RL)] = buf[swz<V>(g * RL + p)];
+        for (int p = 0; p < RL; ++p) x[bitrev(p, RL)] = buf[sidx<V>(g * RL + p)];
         dit<RL>(x);
 #pragma unroll
-        for (int q = 0; q < RL; ++q) buf[swz<V>(g * RL + q)] = x[q];
+        for (int q = 0; q < RL; ++q) buf[sidx<V>(g * RL + q)] = x[q];
     }
     __syncthreads();
     middle_inv<G.np() - 2, LOGLC, R, NT>(buf, twt);
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(NT, 1) mp_inv(const MPParams<T> P, int64_t r) 
         V x[R];
 #pragma unroll
         for (int p = 0; p < R; ++p) {
-            const V yy = buf[swz<V>(o + p * S0)];
+            const V yy = buf[sidx<V>(o + p * S0)];
             x[bitrev(p, R)] = (p == 0) ? yy : cmulc(yy, wp[p]);
         }
         dit_halfout<R>(x);
@@ -337,7 +337,7 @@ int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjo
     P.Y = P.W + (size_t)chunk * P.L / 2;
     P.r0 = reinterpret_cast<T*>(P.Y + (size_t)chunk * P.L);
 
-    constexpr size_t smem_pass = (size_t)(LC + G.twp_len()) * sizeof(V);
+    constexpr size_t smem_pass = (size_t)(padded_len<V>(LC) + G.twp_len()) * sizeof(V);
     const size_t smem_cross = (size_t)(16 * (P.C + 1) + P.C / 2) * sizeof(V);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;

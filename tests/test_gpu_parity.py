@@ -202,7 +202,7 @@ def test_error_paths(tdh):
     assert tdh.lib().tdh_plan_execute(plan._h, ctypes.c_void_p(buf.data_ptr()),
                                       ctypes.c_void_p(buf.data_ptr() + 1024), 0, None) == 0
     with pytest.raises(tdh.TdhError):
-        tdh.Plan("jac2jac", 100, params=(0.1, -0.3, 0.0, 0.0))
+        tdh.Plan("jac2jac", 100, params=(-0.5, -0.5, 0.25, -0.5))  # Case 3: not built
     with pytest.raises(tdh.TdhError):
         tdh.Plan("ultra2ultra", 100, params=(-1.0, 0.5))
     y = plan.execute(x)
