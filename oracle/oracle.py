@@ -127,10 +127,14 @@ def hankel(h, n, j0=0):
     return h[idx[:, None] + idx[None, :]]
 
 
-def first_index(kind):
-    """Index where the positive semidefinite Hankel block starts (Sec. 5.1: row 0 of
-    Chebyshev-to-Legendre is applied directly)."""
-    return 1 if kind == CHEB2LEG else 0
+def first_index(kind, params=None):
+    """Index where the positive semidefinite Hankel block starts: row 0 is applied directly for
+    Chebyshev-to-Legendre (Sec. 5.1) and for Jacobi Case 3, a + b <= -1 (Sec. 5.3)."""
+    if kind == CHEB2LEG:
+        return 1
+    if kind == JAC and params is not None and params[0] + params[1] <= -1.0:
+        return 1
+    return 0
 
 
 # ---------------------------------------------------------------- pivoted Cholesky
@@ -198,7 +202,7 @@ def hankel_factors(kind, params, n, tol, kmax=None):
     H[j0:, j0:] ~ sum_r u_r u_r^T.
     """
     t, h, d1, d2 = split(kind, params, n)
-    j0 = first_index(kind)
+    j0 = first_index(kind, params)
     idx = np.arange(j0, n)
     ells, a, piv = pivoted_cholesky(lambda p: h[idx + idx[p]], h[2 * idx], tol, kmax)
     u = np.zeros((len(a), n))

@@ -13,7 +13,7 @@
  *   LEG2CHEB   eq. (M)            M_jk
  *   CHEB2LEG   eq. (FormulaL)     L_jk
  *   ULTRA      eq. (UltraSconversion), Sec. 5.2
- *   JAC        the Case-2 Jacobi formula of Sec. 5.3 (beta = delta)
+ *   JAC        the Jacobi formula of Sec. 5.3 (beta = delta), Cases 2 and 3
  *   LAG        the Laguerre formula of Sec. 5.4
  * together with the paper's diagonal/Toeplitz/Hankel split of each (eq. (Decomposition),
  * Sec. 5.1, 5.2, 5.3), exported separately so that tests can check the split identity.
@@ -147,7 +147,8 @@ typedef struct {
     dd* E1;       /* JAC: normalised row factor, j in [0, n)     */
     dd* E2;       /* JAC: normalised column factor, k in [0, n)  */
     dd* G;        /* JAC: normalised Hankel factor, q in [0, 2n) */
-    dd c_row0, c_rest; /* LEG2CHEB constants 1/pi and 2/pi */
+    dd c_row0, c_rest; /* LEG2CHEB constants 1/pi and 2/pi; JAC: constant factor */
+    int case3;         /* JAC with a + b <= -1 (factors normalised at index 1) */
     dd sqrtpi;
 } tables;
 
@@ -229,16 +230,37 @@ static int build_tables(tables* tb, int kind, const double* prm, int64_t n) {
             }
             tb->E1[j] = dd_mul(F, dd_add(dd_from(2.0 * (double)j), dd_from(s)));
         }
-        /* Column factor Gamma(k+b+1)/Gamma(k+a+b+1), normalised by its k = 0 value. */
-        if (n > 0) tb->E2[0] = dd_from(1.0);
-        for (int64_t k = 0; k + 1 < n; ++k)
-            tb->E2[k + 1] = dd_div(dd_mul(tb->E2[k], dd_add(dd_from((double)k), dd_from(b + 1.0))),
-                                   dd_add(dd_from((double)k), dd_from(a + b + 1.0)));
-        /* Hankel factor Gamma(q+a+b+1)/Gamma(q+s+1), normalised by its q = 0 value. */
-        tb->G[0] = dd_from(1.0);
-        for (int64_t q = 0; q + 1 < 2 * n; ++q)
-            tb->G[q + 1] = dd_div(dd_mul(tb->G[q], dd_add(dd_from((double)q), dd_from(a + b + 1.0))),
-                                  dd_add(dd_from((double)q), dd_from(s + 1.0)));
+        if (a + b + 1.0 > 0.0) {
+            /* Column factor Gamma(k+b+1)/Gamma(k+a+b+1), normalised by its k = 0 value. */
+            if (n > 0) tb->E2[0] = dd_from(1.0);
+            for (int64_t k = 0; k + 1 < n; ++k)
+                tb->E2[k + 1] = dd_div(dd_mul(tb->E2[k], dd_add(dd_from((double)k), dd_from(b + 1.0))),
+                                       dd_add(dd_from((double)k), dd_from(a + b + 1.0)));
+            /* Hankel factor Gamma(q+a+b+1)/Gamma(q+s+1), normalised by its q = 0 value. */
+            tb->G[0] = dd_from(1.0);
+            for (int64_t q = 0; q + 1 < 2 * n; ++q)
+                tb->G[q + 1] = dd_div(dd_mul(tb->G[q], dd_add(dd_from((double)q), dd_from(a + b + 1.0))),
+                                      dd_add(dd_from((double)q), dd_from(s + 1.0)));
+            tb->c_rest = dd_from(1.0);
+            tb->case3 = 0;
+        } else {
+            /* Case 3 (a + b <= -1): the column and Hankel factors touch Gamma(a+b+1) at index
+               0, where they cancel (A_00 = 1).  Normalise them at index 1 instead; their values
+               there multiply to Gamma(s+1)/Gamma(b+1) * Gamma(b+2)/Gamma(s+2) = (b+1)/(s+1),
+               kept as a separate constant.  Entries with index 0 of these factors are unused. */
+            tb->E2[0] = dd_from(0.0);
+            if (n > 1) tb->E2[1] = dd_from(1.0);
+            for (int64_t k = 1; k + 1 < n; ++k)
+                tb->E2[k + 1] = dd_div(dd_mul(tb->E2[k], dd_add(dd_from((double)k), dd_from(b + 1.0))),
+                                       dd_add(dd_from((double)k), dd_from(a + b + 1.0)));
+            tb->G[0] = dd_from(0.0);
+            if (2 * n > 1) tb->G[1] = dd_from(1.0);
+            for (int64_t q = 1; q + 1 < 2 * n; ++q)
+                tb->G[q + 1] = dd_div(dd_mul(tb->G[q], dd_add(dd_from((double)q), dd_from(a + b + 1.0))),
+                                      dd_add(dd_from((double)q), dd_from(s + 1.0)));
+            tb->c_rest = dd_div(dd_from(b + 1.0), dd_from(s + 1.0));
+            tb->case3 = 1;
+        }
         return 0;
     }
     if (kind == K_LAG) {
@@ -298,8 +320,10 @@ static inline dd entry(const tables* tb, int64_t j, int64_t k) {
         return dd_mul(c, dd_mul(tb->P[(k - j) / 2], tb->Q[(k + j) / 2]));
     }
     case K_JAC: {
-        /* Sec. 5.3 Case 2, normalised factors: E1(j) E2(k) T(k-j) G(k+j). */
-        return dd_mul(dd_mul(tb->E1[j], tb->E2[k]), dd_mul(tb->P[k - j], tb->G[k + j]));
+        /* Sec. 5.3, normalised factors: c E1(j) E2(k) T(k-j) G(k+j); A_00 = 1. */
+        if (tb->case3 && k == 0) return dd_from(1.0);
+        dd v = dd_mul(dd_mul(tb->E1[j], tb->E2[k]), dd_mul(tb->P[k - j], tb->G[k + j]));
+        return tb->case3 ? dd_mul(v, tb->c_rest) : v;
     }
     case K_LAG: {
         /* Sec. 5.4: Gamma(k-j+d) / (Gamma(d) Gamma(k-j+1)). */
@@ -389,7 +413,8 @@ int tdho_entries(int kind, const double* prm, int64_t n, int64_t j0, int64_t j1,
  *            t_m = Gamma((m-1)/2)/Gamma((m+2)/2) (m even), h_s = Gamma(s/2)/Gamma((s+3)/2), h_0 = 1.
  * ULTRA      Sec. 5.2: D1 = diag(j + l2), D2 = I, t_m = P'(m/2) (m even),
  *            h_s = Q'(s/2); at odd s, Q'(s/2) starts from Gamma values computed in double.
- * JAC        Sec. 5.3: D1 = E1, D2 = E2, t = T, h = G.
+ * JAC        Sec. 5.3: D1 = E1, D2 = E2, t = T, h = G (Case 3: normalised at index 1, index-0
+ *            entries of D2 and h unused and set to 0, the constant (b+1)/(s+1) in D1).
  * LAG        Sec. 5.4: D1 = D2 = I, t = T, h = 1.
  */
 int tdho_split(int kind, const double* prm, int64_t n, double* t, double* h, double* d1,
@@ -456,9 +481,13 @@ int tdho_split(int kind, const double* prm, int64_t n, double* t, double* h, dou
         break;
     }
     case K_JAC: {
+        /* Case 3: row and column 0 are applied directly (A_00 = 1); the constant goes to D1. */
         for (int64_t m = 0; m < n; ++m) t[m] = dd_round(tb.P[m]);
         for (int64_t s = 0; s < nh; ++s) h[s] = dd_round(tb.G[s]);
-        for (int64_t j = 0; j < n; ++j) { d1[j] = dd_round(tb.E1[j]); d2[j] = dd_round(tb.E2[j]); }
+        for (int64_t j = 0; j < n; ++j) {
+            d1[j] = dd_round(tb.case3 ? dd_mul(tb.E1[j], tb.c_rest) : tb.E1[j]);
+            d2[j] = dd_round(tb.E2[j]);
+        }
         break;
     }
     case K_LAG: {

@@ -28,6 +28,8 @@ CASES = [
     ("jac_case2_paper", oracle.JAC, (0.0, 0.5, -0.25), ("jacobi", Fr(0), Fr(1, 2)), ("jacobi", Fr(-1, 4), Fr(1, 2))),
     ("jac_to_cheb", oracle.JAC, (0.0, -0.5, -0.5), ("jacobi", Fr(0), Fr(-1, 2)), ("jacobi", Fr(-1, 2), Fr(-1, 2))),
     ("jac_case1", oracle.JAC, (0.5, 0.25, 1.5), ("jacobi", Fr(1, 2), Fr(1, 4)), ("jacobi", Fr(3, 2), Fr(1, 4))),
+    ("jac_case3_cheb", oracle.JAC, (-0.5, -0.5, 0.25), ("jacobi", Fr(-1, 2), Fr(-1, 2)), ("jacobi", Fr(1, 4), Fr(-1, 2))),
+    ("jac_case3", oracle.JAC, (-0.6, -0.7, -0.2), ("jacobi", Fr(-3, 5), Fr(-7, 10)), ("jacobi", Fr(-1, 5), Fr(-7, 10))),
     ("lag", oracle.LAG, (0.5, -0.25), ("laguerre", Fr(1, 2)), ("laguerre", Fr(-1, 4))),
 ]
 
@@ -62,7 +64,7 @@ def test_split_identity(name, kind, params, src, dst):
     k = np.arange(n)[None, :]
     T = np.where(k >= j, t[np.clip(k - j, 0, n - 1)], 0.0)
     A = d1[:, None] * T * h[j + k] * d2[None, :]
-    j0 = oracle.first_index(kind)
+    j0 = oracle.first_index(kind, params)
     sub = (slice(j0, n), slice(j0, n))
     assert np.allclose(A[sub], exact[sub], rtol=2e-15, atol=1e-300)
 
@@ -199,12 +201,14 @@ def test_hankel_moment_integrals():
 
 
 @pytest.mark.parametrize("kind,params", [(oracle.LEG2CHEB, None), (oracle.CHEB2LEG, None),
-                                         (oracle.ULTRA, (0.75, 1.25)), (oracle.JAC, (0.1, -0.3, 0.0))])
+                                         (oracle.ULTRA, (0.75, 1.25)), (oracle.JAC, (0.1, -0.3, 0.0)),
+                                         (oracle.JAC, (-0.6, -0.7, -0.2))])
 def test_hankel_psd(kind, params):
-    """The Hankel part is positive semidefinite (on indices >= 1 for Chebyshev-to-Legendre)."""
+    """The Hankel part is positive semidefinite (on indices >= 1 for Chebyshev-to-Legendre and
+    Jacobi Case 3, Sec. 5.1 and 5.3)."""
     n = 160
     _, h, _, _ = oracle.split(kind, params, n)
-    H = oracle.hankel(h, n, oracle.first_index(kind))
+    H = oracle.hankel(h, n, oracle.first_index(kind, params))
     ev = np.linalg.eigvalsh(H)
     assert ev.min() > -1e-14 * ev.max()
 
