@@ -35,6 +35,7 @@ extern "C" {
 #define TDH_CHEB2LEG    1 /* Chebyshev -> Legendre, eq. (FormulaL), split Sec. 5.1           */
 #define TDH_ULTRA2ULTRA 2 /* ultraspherical C^(l1) -> C^(l2), Sec. 5.2, p = {l1, l2}          */
 #define TDH_JAC2JAC     3 /* Jacobi P^(a,b) -> P^(g,d), Sec. 5.3, p = {a, b, g, d}           */
+#define TDH_LAG2LAG     4 /* generalised Laguerre L^(a1) -> L^(a2), Sec. 5.4, p = {a1, a2}   */
 
 /* ---------------------------------------------------------------- execute precisions */
 #define TDH_FP64  0 /* float64 in/out, float64 FFT                                             */
@@ -57,7 +58,7 @@ extern "C" {
 typedef struct tdh_plan_s* tdh_plan_t; /* opaque; immutable after creation */
 
 typedef struct {
-    double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; ignored otherwise   */
+    double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; LAG {a1, a2}         */
     int prec;     /* TDH_FP64 or TDH_FP32: the precision of plan_execute's in/out and FFTs  */
     int flags;    /* TDH_FLAG_* (none defined yet; pass 0)                                  */
     int64_t kmax; /* cap on the rank of each Hankel factorisation; 0 selects 128            */

@@ -76,7 +76,10 @@ int build_step(Step& st, double tol, int64_t kmax, int prec, cudaStream_t s) {
     TDH_TRY(dev_alloc_t(&st.d1, n));
     TDH_TRY(dev_alloc_t(&st.d2, n));
     TDH_TRY(symbols_launch(st.kind, n, st.p, st.t, st.h, st.d1, st.d2, s));
-    st.j0 = (st.kind == TDH_CHEB2LEG) ? 1 : 0;
+    // row 0 applied directly, Hankel block on indices >= 1: Chebyshev-to-Legendre (Sec. 5.1)
+    // and Jacobi Case 3, a + b <= -1 (Sec. 5.3)
+    st.j0 = (st.kind == TDH_CHEB2LEG || (st.kind == TDH_JAC2JAC && !(st.p[0] + st.p[1] > -1.0)))
+                ? 1 : 0;
     st.K = 0;
     if (st.j0 < n) {
         int64_t kcap = std::min<int64_t>(kmax, n - st.j0);
@@ -163,8 +166,9 @@ int run(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream,
 }
 
 bool case2(double a, double b, double g) {
-    // Sec. 5.3 Case 2: |a - g| < 1, a != g, a + b > -1
-    return std::fabs(a - g) < 1.0 && a != g && a + b > -1.0;
+    // Sec. 5.3 Case 2 (|a - g| < 1, a != g, a + b > -1) or Case 3 (the same with a + b <= -1)
+    (void)b;
+    return std::fabs(a - g) < 1.0 && a != g;
 }
 
 }  // namespace
@@ -184,7 +188,7 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         return TDH_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (kind < TDH_LEG2CHEB || kind > TDH_JAC2JAC) {
+    if (kind < TDH_LEG2CHEB || kind > TDH_LAG2LAG) {
         set_error("unknown kind %d", kind);
         return TDH_ERR_INVALID_ARG;
     }
@@ -207,8 +211,8 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
             return TDH_ERR_INVALID_ARG;
         }
         if ((b != d && !case2(b, a, d)) || (a != g && !case2(a, d, g))) {
-            set_error("Jacobi conversion is built for chains of Case-2 steps only "
-                      "(|b-d| < 1 with a+b > -1, and |a-g| < 1 with a+d > -1)");
+            set_error("Jacobi conversion is built for chains of Case-2/3 steps "
+                      "(|b-d| < 1 and |a-g| < 1); Case 4 (integer shifts) is not built");
             return TDH_ERR_UNSUPPORTED;
         }
     }
@@ -291,6 +295,19 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
             st.p[1] = l2;
             plan->steps.push_back(st);
         }
+    } else if (kind == TDH_LAG2LAG) {
+        // Sec. 5.4: Toeplitz only (H = all ones, rank 1); no parity structure
+        if (!(params->p[0] > -1.0) || !(params->p[1] > -1.0)) {
+            rc = TDH_ERR_INVALID_ARG;
+            set_error("Laguerre parameters must be > -1");
+        } else if (params->p[0] != params->p[1]) {
+            Step st;
+            st.kind = kind;
+            st.n = n_max;
+            st.full = 1;
+            std::memcpy(st.p, params->p, sizeof(st.p));
+            plan->steps.push_back(st);
+        }
     } else {
         Step st;
         st.kind = kind;
@@ -299,6 +316,7 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         plan->steps.push_back(st);
     }
     for (auto& st : plan->steps) {
+        if (rc != TDH_OK) break;
         rc = build_step(st, tol, kmax, params->prec, s);
         if (rc != TDH_OK) break;
     }

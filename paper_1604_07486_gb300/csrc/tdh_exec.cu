@@ -161,7 +161,7 @@ __global__ void k_cast(const double* __restrict__ in, T* __restrict__ out, int64
     if (i < count) out[i] = (T)in[i];
 }
 
-// row 0 of A = D1 (T o H) D2 (valid for k >= 1), with A_00 = 1 (Sec. 5.1)
+// row 0 of A = D1 (T o H) D2 (valid for k >= 1), with A_00 = 1 (Sec. 5.1, Sec. 5.3 Case 3)
 template <typename T>
 __global__ void k_row0(const double* __restrict__ t, const double* __restrict__ h,
                        const double* __restrict__ d1, const double* __restrict__ d2, int64_t n,
@@ -268,7 +268,7 @@ int prepare_diagonals(Step& st, cudaStream_t s) {
     TDH_TRY(dev_alloc(&st.d2x, sizeof(T) * n));
     k_cast<T><<<blocks_for(n), kThreads, 0, s>>>(st.d1, (T*)st.d1x, n);
     k_cast<T><<<blocks_for(n), kThreads, 0, s>>>(st.d2, (T*)st.d2x, n);
-    if (st.kind == TDH_CHEB2LEG) {
+    if (st.j0 == 1) {
         TDH_TRY(dev_alloc(&st.row0, sizeof(T) * n));
         k_row0<T><<<blocks_for(n), kThreads, 0, s>>>(st.t, st.h, st.d1, st.d2, n, (T*)st.row0);
     }
@@ -281,6 +281,17 @@ int prepare_diagonals(Step& st, cudaStream_t s) {
 template <typename T>
 int dispatch(const Geometry& g, const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
     return P.ragged ? dispatch_ragged(g, P, batch, s) : dispatch_dense(g, P, batch, s);
+}
+
+// out[v][k] = sum_s partial[s][v][k], fixed order (deterministic)
+template <typename T>
+__global__ void k_split_reduce(const T* __restrict__ partial, T* __restrict__ out, int64_t total,
+                               int nsplit) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= total) return;
+    T acc = partial[i];
+    for (int s = 1; s < nsplit; ++s) acc += partial[(int64_t)s * total + i];
+    out[i] = acc;
 }
 
 template <typename T>
@@ -312,7 +323,31 @@ int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int a
     P.list = nullptr;
     P.count = nullptr;
     P.next = nullptr;
-    return dispatch<T>(ex.g, P, batch, s);
+    P.batch = batch;
+    P.partial = nullptr;
+    // A batch too small to fill the GPU: split the rank terms over several clusters per vector
+    // and add the partial results in a second pass.
+    const int64_t clusters = batch * ex.g.C;
+    int64_t nsplit = 1;
+    if (P.K > 1 && 2 * clusters < sm_count())
+        nsplit = std::min<int64_t>(std::min<int64_t>(P.K, 32), sm_count() / clusters);
+    P.nsplit = (int)nsplit;
+    if (nsplit <= 1) return dispatch<T>(ex.g, P, batch, s);
+    const int64_t total = batch * st.n;
+    T* partial = nullptr;
+    TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&partial), sizeof(T) * total * nsplit, s));
+    P.partial = partial;
+    int rc = dispatch<T>(ex.g, P, batch * nsplit, s);
+    if (rc == TDH_OK) {
+        k_split_reduce<T><<<blocks_for(total), kThreads, 0, s>>>(partial, P.out, total, (int)nsplit);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error("split reduce: %s", cudaGetErrorString(e));
+            rc = TDH_ERR_CUDA;
+        }
+    }
+    cudaFreeAsync(partial, s);
+    return rc;
 }
 
 }  // namespace
@@ -447,6 +482,9 @@ int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t
         P.sign_in = 0;
         P.sign_out = 0;
         P.u_stride = ex.u_stride;
+        P.nsplit = 1;
+        P.batch = batch;
+        P.partial = nullptr;
         P.ragged = 1;
         P.offs = offs;
         P.list = list + (int64_t)c * batch;

@@ -90,6 +90,11 @@ struct ExecParams {
     int sign_in;    // multiply input coefficient k by (-1)^k (Jacobi reflection)
     int sign_out;   // multiply output coefficient k by (-1)^k
     int64_t u_stride;  // complex entries between consecutive (rank, k1) rows of u
+    // rank split (small dense batches): cluster (s, v) applies rank terms
+    // [K s / nsplit, K (s+1) / nsplit) of vector v and writes partial[s][v][*]
+    int nsplit;
+    int64_t batch;
+    T* partial;
     // ragged batches: vector v occupies [offs[v], offs[v+1]); this launch converts the
     // vectors list[0 .. *count) of one FFT-length class, taking them from the *next counter
     int ragged;
@@ -239,7 +244,9 @@ template <typename T, int LOGLC, int R, int C, int NT>
 __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* in, T* out,
                                                const int64_t n, const int k1,
                                                typename cx<T>::t* buf, typename cx<T>::t* vbuf,
-                                               const typename cx<T>::t* twt, T* red) {
+                                               const typename cx<T>::t* twt, T* red,
+                                               const int64_t r_begin, const int64_t r_end,
+                                               const bool lead) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
     constexpr int LC = G.LC();
@@ -256,6 +263,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             if (a < n) {
                 T x = in[a];
                 if (P.sign_in && (a & 1)) x = -x;
+                if (P.row0 && !P.adjoint) r0acc += P.row0[a] * x;
                 const T xv = x * P.din[a];
                 v = mk<V>(xv, xv);
             }
@@ -293,7 +301,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
     }
 
 #pragma unroll 1
-    for (int64_t r = 0; r < P.K; ++r) {
+    for (int64_t r = r_begin; r < r_end; ++r) {
         const V* ur = P.u + ((int64_t)r * C + k1) * P.u_stride;
         // ---- forward pass 0: inputs u_r o v (upper half zero), radix R, stride S0
 #pragma unroll
@@ -436,7 +444,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 
     // ---- epilogue: beta = D1 w (forward) / D2 w (adjoint), row 0, write once
     T g0 = T(0);
-    if (P.row0 && P.adjoint) g0 = in[0];
+    if (P.row0 && P.adjoint && lead) g0 = in[0];
 #pragma unroll
     for (int j = 0; j < J0; ++j) {
         const int o = tid + j * NT;
@@ -446,6 +454,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             if (P.full) {
                 if (a < n) {
                     T b = acc[j][q].x * P.dout[a];
+                    if (P.row0 && P.adjoint) b += P.row0[a] * g0;
                     if (P.sign_out && (a & 1)) b = -b;
                     out[a] = b;
                 }
@@ -465,7 +474,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             }
         }
     }
-    if (P.row0 && !P.adjoint) {
+    if (P.row0 && !P.adjoint && lead) {
         // beta_0 = sum_k A_0k alpha_k: block reduction, then across the cluster
         for (int off = 16; off > 0; off >>= 1) r0acc += __shfl_down_sync(0xffffffffu, r0acc, off);
         if ((tid & 31) == 0) red[tid >> 5] = r0acc;
@@ -516,9 +525,18 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
     if constexpr (C > 1) k1 = (int)cg::this_cluster().block_rank();
     for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
     if constexpr (!RAGGED) {
-        const int64_t vec = blockIdx.x / C;
-        convert_vector<T, LOGLC, R, C, NT>(P, P.in + vec * P.n, P.out + vec * P.n, P.n, k1, buf,
-                                           vbuf, twt, red);
+        const int64_t cid = blockIdx.x / C;
+        const int64_t vec = cid % P.batch;
+        const int64_t sp = cid / P.batch;
+        T* outp = P.out + vec * P.n;
+        int64_t r0 = 0, r1 = P.K;
+        if (P.nsplit > 1) {
+            r0 = P.K * sp / P.nsplit;
+            r1 = P.K * (sp + 1) / P.nsplit;
+            outp = P.partial + (sp * P.batch + vec) * P.n;
+        }
+        convert_vector<T, LOGLC, R, C, NT>(P, P.in + vec * P.n, outp, P.n, k1, buf, vbuf, twt,
+                                           red, r0, r1, sp == 0);
     } else {
         __shared__ int slot[2];
         const int count = *P.count;
@@ -538,7 +556,7 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
             const int64_t off = P.offs[vec];
             const int64_t n = P.offs[vec + 1] - off;
             convert_vector<T, LOGLC, R, C, NT>(P, P.in + off, P.out + off, n, k1, buf, vbuf, twt,
-                                               red);
+                                               red, 0, P.K, true);
         }
         if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its slot is read
     }

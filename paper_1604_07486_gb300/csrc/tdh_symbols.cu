@@ -12,6 +12,7 @@
 // carries the rounding of pow and exp, a few ulp.
 #include <cmath>
 #include <cstdarg>
+#include <vector>
 
 #include "tdh_internal.cuh"
 
@@ -210,11 +211,36 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
             set_error("Jacobi parameters must be > -1");
             return TDH_ERR_INVALID_ARG;
         }
-        if (!(std::fabs(a - g) < 1.0) || is_nonpos_integer(a - g) || !(a + b > -1.0)) {
-            set_error("tdh_symbols: Jacobi split needs Case 2 (|a - g| < 1, a != g, a + b > -1)");
+        if (!(std::fabs(a - g) < 1.0) || is_nonpos_integer(a - g)) {
+            set_error("tdh_symbols: Jacobi split needs |a - g| < 1, a != g (Cases 2 and 3)");
             return TDH_ERR_UNSUPPORTED;
         }
         TDH_TRY(launch_table(ratio_spec(a - g, 1.0, 0.0, 1.0, 1.0 / std::tgamma(a - g)), n, t, st));
+        if (!(a + b > -1.0)) {
+            // Case 3 (a + b <= -1): E2 and G touch Gamma(a+b+1) at index 0, where the two cancel
+            // (A_00 = 1, applied directly).  Normalise both at index 1; their product there is
+            // Gamma(s+1)/Gamma(b+1) * Gamma(b+2)/Gamma(s+2) = (b+1)/(s+1), carried by D1.
+            // Index-0 entries of h and d2 are unused and set to 0.
+            TableSpec hs = ratio_spec(a + b + 1.0, s + 1.0, 0.0, 1.0,
+                                      std::tgamma(s + 2.0) / std::tgamma(a + b + 2.0));
+            hs.special_i = 0;
+            hs.special_v = 0.0;
+            TDH_TRY(launch_table(hs, nh, h, st));
+            TableSpec e1 = ratio_spec(s, b + 1.0, 0.0, 1.0,
+                                      (b + 1.0) / (s + 1.0) * std::tgamma(b + 1.0) / std::tgamma(s + 1.0));
+            e1.use_lin = 1;
+            e1.lin0 = s;
+            e1.lin1 = 2.0;
+            e1.special_i = 0;
+            e1.special_v = (b + 1.0) / (s + 1.0);
+            TDH_TRY(launch_table(e1, n, d1, st));
+            TableSpec e2 = ratio_spec(b + 1.0, a + b + 1.0, 0.0, 1.0,
+                                      std::tgamma(a + b + 2.0) / std::tgamma(b + 2.0));
+            e2.special_i = 0;
+            e2.special_v = 0.0;
+            TDH_TRY(launch_table(e2, n, d2, st));
+            return TDH_OK;
+        }
         TDH_TRY(launch_table(ratio_spec(a + b + 1.0, s + 1.0, 0.0, 1.0,
                                         std::tgamma(s + 1.0) / std::tgamma(a + b + 1.0)),
                              nh, h, st));
@@ -228,6 +254,34 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
         TDH_TRY(launch_table(ratio_spec(b + 1.0, a + b + 1.0, 0.0, 1.0,
                                         std::tgamma(a + b + 1.0) / std::tgamma(b + 1.0)),
                              n, d2, st));
+        return TDH_OK;
+    }
+    case TDH_LAG2LAG: {
+        // Sec. 5.4: A_jk = Gamma(k-j+d)/(Gamma(d) Gamma(k-j+1)), d = a1 - a2: a Toeplitz matrix,
+        // i.e. T o H with H the matrix of all ones; D1 = D2 = I.
+        const double d = p[0] - p[1];
+        if (!(p[0] > -1.0) || !(p[1] > -1.0)) {
+            set_error("Laguerre parameters must be > -1");
+            return TDH_ERR_INVALID_ARG;
+        }
+        if (is_nonpos_integer(d)) {
+            // 1/Gamma(d) = 0 with poles in the numerator: t_m = (-1)^m C(-d, m), m <= -d
+            const int M = (int)(-d);
+            std::vector<double> tm((size_t)std::min<int64_t>(n, M + 1));
+            double c = 1.0;
+            for (int m = 0; m < (int)tm.size(); ++m) {
+                tm[m] = (m % 2 ? -c : c);
+                c = c * (double)(M - m) / (double)(m + 1);
+            }
+            TDH_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * n, st));
+            TDH_CUDA(cudaMemcpyAsync(t, tm.data(), sizeof(double) * tm.size(), cudaMemcpyHostToDevice, st));
+            TDH_CUDA(cudaStreamSynchronize(st));
+        } else {
+            TDH_TRY(launch_table(ratio_spec(d, 1.0, 0.0, 1.0, 1.0 / std::tgamma(d)), n, t, st));
+        }
+        TDH_TRY(launch_table(linear_spec(1.0, 1.0, 0.0), nh, h, st));
+        TDH_TRY(launch_table(linear_spec(1.0, 1.0, 0.0), n, d1, st));
+        TDH_TRY(launch_table(linear_spec(1.0, 1.0, 0.0), n, d2, st));
         return TDH_OK;
     }
     default:

@@ -202,7 +202,7 @@ def test_error_paths(tdh):
     assert tdh.lib().tdh_plan_execute(plan._h, ctypes.c_void_p(buf.data_ptr()),
                                       ctypes.c_void_p(buf.data_ptr() + 1024), 0, None) == 0
     with pytest.raises(tdh.TdhError):
-        tdh.Plan("jac2jac", 100, params=(-0.5, -0.5, 0.25, -0.5))  # Case 3: not built
+        tdh.Plan("jac2jac", 100, params=(0.1, 0.0, 1.6, 0.0))  # Case 4: not built
     with pytest.raises(tdh.TdhError):
         tdh.Plan("ultra2ultra", 100, params=(-1.0, 0.5))
     y = plan.execute(x)
@@ -217,6 +217,9 @@ JAC_CASES = [
     ((0.1, -0.3, 0.0, 0.0), "reflection chain: (0.1,-0.3) -> (0.1,0) -> (0,0)"),
     ((0.0, 2 ** 0.5 / 2, -0.25, 2 ** 0.5 / 2), "the paper's Fig. 6 workload"),
     ((-0.4, -0.5, 0.25, -0.5), "near the Chebyshev weight"),
+    ((-0.5, -0.5, 0.25, -0.5), "Case 3 from the Chebyshev weight"),
+    ((-0.6, -0.7, -0.2, -0.7), "Case 3"),
+    ((-0.5, -0.5, 0.0, 0.0), "chain with a Case-3 reflection step"),
 ]
 
 
@@ -294,9 +297,9 @@ def test_config4_ultraspherical_n2p20_b16(tdh, prec):
     assert err <= TOL[prec]
 
 
-def test_jacobi_case3_reported_unsupported(tdh):
-    """a + b <= -1 (Case 3) and |a - g| > 1 (Case 4) are not built: a clear error, no result."""
-    for params in [(-0.5, -0.5, 0.25, -0.5), (0.1, 0.0, 1.6, 0.0)]:
+def test_jacobi_case4_reported_unsupported(tdh):
+    """|a - g| > 1 (Case 4: integer shifts first) is not built: a clear error, no result."""
+    for params in [(0.1, 0.0, 1.6, 0.0), (0.1, 0.0, -0.95, 0.0)]:
         with pytest.raises(tdh.TdhError) as e:
             tdh.Plan("jac2jac", 100, params=params)
         assert e.value.code == -2
@@ -395,3 +398,36 @@ def test_config4_supplementary_ultraspherical_case2_n2p20(tdh):
     ref = oracle.matvec(oracle.ULTRA, (0.25, 1.0), alpha, rows=rows)
     err = (np.abs(y[:, rows] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
     assert err <= 5e-6, err
+
+
+def test_jacobi_chebyshev_weight_equals_cheb2leg(tdh):
+    """T_k = P_k^(-1/2,-1/2) / P_k^(-1/2,-1/2)(1) (Sec. 5.3): Jacobi (-1/2,-1/2) -> (0,0) of
+    c_k / P_k(1) equals Chebyshev -> Legendre of c (two different plans, same answer)."""
+    torch = _torch()
+    n = 3000
+    c = workloads.coefficients(n, 2, decay=1.0, seed=9)
+    hi, _ = oracle.lambda_dd(2 * n + 2)
+    pk1 = hi[2 * np.arange(n)] / np.sqrt(np.pi)  # P_k^(-1/2,-1/2)(1) = Lambda(k)/sqrt(pi)
+    pj = tdh.Plan("jac2jac", n, prec="fp64", tol=1e-17, params=(-0.5, -0.5, 0.0, 0.0))
+    pc = tdh.Plan("cheb2leg", n, prec="fp64", tol=1e-17)
+    yj = pj.execute(torch.tensor(c / pk1, device="cuda")).cpu().numpy()
+    yc = pc.execute(torch.tensor(c, device="cuda")).cpu().numpy()
+    assert _rel_err(yj, yc, c) <= 1e-12
+
+
+# ------------------------------------------------------------------------------- Laguerre
+
+@pytest.mark.parametrize("params", [(0.5, -0.25), (0.3, 1.7), (2.0, 0.0), (0.0, 2.0)],
+                         ids=["d=0.75", "d=-1.4", "d=2", "d=-2"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_laguerre(tdh, params, prec):
+    """Sec. 5.4: a pure Toeplitz conversion (H all ones, rank 1).  Tolerance relative to the
+    largest Toeplitz entry, which grows like m^(d-1)."""
+    n = 3000
+    tol = 1e-15 if prec == "fp64" else 1e-7
+    plan, alpha, y = _run(tdh, "lag2lag", n, 2, prec, tol, decay=1.0, params=params)
+    assert plan.K == 1
+    ref = oracle.matvec(oracle.LAG, params, alpha)
+    t = oracle.split(oracle.LAG, params, n)[0]
+    scale = max(1.0, np.abs(t).max())
+    assert _rel_err(y, ref, alpha) <= TOL[prec] * scale
