@@ -10,10 +10,12 @@ conversion, Clenshaw evaluation, Hankel moment integrals, L M = I, the K = 27 ra
 Sec. 2.1, and the full-update Cholesky form), except ``fast_matvec``, which is a CPU
 timing reference and is never used as parity truth.
 """
-from .oracle import (CHEB2LEG, JAC, LAG, LEG2CHEB, ULTRA, entries, fast_matvec, first_index,
-                     hankel, hankel_factors, jac2jac, lambda_dd, matvec, pivoted_cholesky,
-                     pivoted_cholesky_full, split, threads)
+from .oracle import (CHEB2LEG, JAC, LAG, LEG2CHEB, ULTRA, cheb2jac, chebyshev_normalisation,
+                     entries, fast_matvec, first_index, hankel, hankel_factors, jac2cheb,
+                     jac2jac, lambda_dd, matvec, pivoted_cholesky, pivoted_cholesky_full, split,
+                     threads)
 
-__all__ = ["CHEB2LEG", "JAC", "LAG", "LEG2CHEB", "ULTRA", "entries", "fast_matvec",
-           "first_index", "hankel", "hankel_factors", "jac2jac", "lambda_dd", "matvec",
-           "pivoted_cholesky", "pivoted_cholesky_full", "split", "threads"]
+__all__ = ["CHEB2LEG", "JAC", "LAG", "LEG2CHEB", "ULTRA", "cheb2jac", "chebyshev_normalisation",
+           "entries", "fast_matvec", "first_index", "hankel", "hankel_factors", "jac2cheb",
+           "jac2jac", "lambda_dd", "matvec", "pivoted_cholesky", "pivoted_cholesky_full",
+           "split", "threads"]

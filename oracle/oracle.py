@@ -14,7 +14,12 @@ matrices" (arXiv:1604.07486).
   prose of Sec. 2.1 describes (apply each earlier Cholesky step to column p_r).
 * ``pivoted_cholesky_full`` is the O(K N^2) full-update form, eq. (FirstCholeskyStep).
 * ``jac2jac`` composes the Case-2 formula with the reflection of Sec. 5.3 when
-  beta != delta (reading: P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x)).
+  beta != delta (reading: P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x)).  The closed form of
+  Sec. 5.3 holds for every parameter pair (its Gamma ratios come from recurrences, which
+  continue through integer differences), so the oracle takes no integer steps: Cases 1 and
+  4 are the same formula.
+* ``jac2cheb`` / ``cheb2jac`` use T_k = P_k^(-1/2,-1/2) / P_k^(-1/2,-1/2)(1) (Sec. 5.3,
+  end): a Jacobi (-1/2, -1/2) conversion and a diagonal scaling.
 * ``fast_matvec`` is the outline of Fig. 1 in float64 with numpy's FFT as the Toeplitz
   step; it is a CPU timing reference only, never the parity truth.
 """
@@ -220,12 +225,40 @@ def jac2jac(x, a, b, g, d, rows=None):
     flip signs, convert (b, a) -> (d, a), flip back, then convert (a, d) -> (g, d).
     """
     x = np.asarray(x, dtype=np.float64)
+    if b == d and a == g:
+        return x.copy() if rows is None else x[..., np.asarray(rows)].copy()
     if b == d:
         return matvec(JAC, (a, b, g), x, rows=rows)
     n = x.shape[-1]
     sign = (-1.0) ** np.arange(n)
     y = sign * matvec(JAC, (b, a, d), sign * x)
+    if a == g:
+        return y if rows is None else y[..., np.asarray(rows)]
     return matvec(JAC, (a, d, g), y, rows=rows)
+
+
+def chebyshev_normalisation(n):
+    """P_k^(-1/2,-1/2)(1) = Gamma(k + 1/2) / (Gamma(1/2) Gamma(k + 1)) = Lambda(k)/sqrt(pi),
+    k < n (DLMF 18.6.1), from the double-double Lambda table."""
+    hi, lo = lambda_dd(2 * n)
+    return (hi[0::2] + lo[0::2]) / np.sqrt(np.pi)
+
+
+def jac2cheb(x, a, b, rows=None):
+    """Jacobi (a, b) -> Chebyshev: convert to Jacobi (-1/2, -1/2), then c_k <- c_k
+    P_k^(-1/2,-1/2)(1), since P_k^(-1/2,-1/2) = P_k^(-1/2,-1/2)(1) T_k (Sec. 5.3, end)."""
+    x = np.asarray(x, dtype=np.float64)
+    s = chebyshev_normalisation(x.shape[-1])
+    y = jac2jac(x, a, b, -0.5, -0.5, rows=rows)
+    return y * (s if rows is None else s[np.asarray(rows)])
+
+
+def cheb2jac(x, a, b, rows=None):
+    """Chebyshev -> Jacobi (a, b): c_k <- c_k / P_k^(-1/2,-1/2)(1), then Jacobi
+    (-1/2, -1/2) -> (a, b)."""
+    x = np.asarray(x, dtype=np.float64)
+    s = chebyshev_normalisation(x.shape[-1])
+    return jac2jac(x / s, -0.5, -0.5, a, b, rows=rows)
 
 
 # ---------------------------------------------------------------- CPU timing reference

@@ -31,6 +31,15 @@ CASES = [
     ("jac_case3_cheb", oracle.JAC, (-0.5, -0.5, 0.25), ("jacobi", Fr(-1, 2), Fr(-1, 2)), ("jacobi", Fr(1, 4), Fr(-1, 2))),
     ("jac_case3", oracle.JAC, (-0.6, -0.7, -0.2), ("jacobi", Fr(-3, 5), Fr(-7, 10)), ("jacobi", Fr(-1, 5), Fr(-7, 10))),
     ("lag", oracle.LAG, (0.5, -0.25), ("laguerre", Fr(1, 2)), ("laguerre", Fr(-1, 4))),
+    # integer and larger-than-one differences: the same closed forms (Sec. 5.2 Cases 1/3,
+    # Sec. 5.3 Cases 1/4), downward and upward
+    ("ultra_case1_down", oracle.ULTRA, (1.25, 0.25), ("gegenbauer", Fr(5, 4)), ("gegenbauer", Fr(1, 4))),
+    ("ultra_case3_down", oracle.ULTRA, (2.25, 0.75), ("gegenbauer", Fr(9, 4)), ("gegenbauer", Fr(3, 4))),
+    ("jac_case1_down", oracle.JAC, (1.5, 0.25, 0.5), ("jacobi", Fr(3, 2), Fr(1, 4)), ("jacobi", Fr(1, 2), Fr(1, 4))),
+    ("jac_case1_two", oracle.JAC, (0.5, 0.25, 2.5), ("jacobi", Fr(1, 2), Fr(1, 4)), ("jacobi", Fr(5, 2), Fr(1, 4))),
+    ("jac_case4_up", oracle.JAC, (0.25, 0.0, 1.75), ("jacobi", Fr(1, 4), Fr(0)), ("jacobi", Fr(7, 4), Fr(0))),
+    ("jac_case4_down", oracle.JAC, (1.75, 0.5, -0.5), ("jacobi", Fr(7, 4), Fr(1, 2)), ("jacobi", Fr(-1, 2), Fr(1, 2))),
+    ("jac_case4_to_case3", oracle.JAC, (0.625, -0.875, -0.75), ("jacobi", Fr(5, 8), Fr(-7, 8)), ("jacobi", Fr(-3, 4), Fr(-7, 8))),
 ]
 
 
@@ -235,3 +244,55 @@ def test_sampled_rows_equal_dense():
     full = oracle.matvec(oracle.CHEB2LEG, None, x)
     part = oracle.matvec(oracle.CHEB2LEG, None, x, rows=rows)
     assert np.array_equal(full[:, rows], part)
+
+
+@pytest.mark.parametrize("a,b", [(Fr(1, 4), Fr(-1, 3)), (Fr(0), Fr(-1, 2)), (Fr(3, 2), Fr(1, 4)),
+                                 (Fr(-1, 2), Fr(-1, 2))])
+def test_jac2cheb_cheb2jac_exact(a, b):
+    """Jacobi <-> Chebyshev through T_k = P_k^(-1/2,-1/2) / P_k^(-1/2,-1/2)(1) (Sec. 5.3, end)
+    equals the exact conversion between the two families built from their recurrences."""
+    n = 12
+    exact_jc = polys.to_float(_exact(("jacobi", a, b), ("chebyshev",), n))
+    exact_cj = polys.to_float(_exact(("chebyshev",), ("jacobi", a, b), n))
+    I = np.eye(n)
+    A = np.stack([oracle.jac2cheb(e, float(a), float(b)) for e in I], axis=1)
+    B = np.stack([oracle.cheb2jac(e, float(a), float(b)) for e in I], axis=1)
+    assert np.abs(A - exact_jc).max() < 2e-14 * np.abs(exact_jc).max()
+    assert np.abs(B - exact_cj).max() < 2e-14 * np.abs(exact_cj).max()
+
+
+def _bidiagonal(n, off, diag, sup):
+    S = [[Fr(0)] * n for _ in range(n)]
+    for j in range(n):
+        S[j][j] = diag(j)
+        if j + off < n:
+            S[j][j + off] = sup(j)
+    return S
+
+
+def test_sparse_factor_readings():
+    """The sparse factors the GPU path applies for integer steps, checked exactly.
+
+    Sec. 5.2, eq. (sparseFactorization): (S_l)_jj = l/(l+j), (S_l)_{j,j+2} = -l/(l+j+2) maps
+    C^(l) coefficients to C^(l+1) coefficients.  Sec. 5.3 Case 1: S_(a,b) maps (a, b)
+    coefficients to (a+1, b) coefficients with diagonal (j+a+b+1)/(2j+a+b+1) (1 at j = 0)
+    and superdiagonal -(j+b+1)/(2j+a+b+3).  The paper prints the superdiagonal numerator
+    as j+a+1, which is the factor for raising b instead (up to sign); the exact conversion
+    decides for j+b+1, and the printed form fails whenever a != b."""
+    n = 10
+    for lam in (Fr(1, 4), Fr(3, 2)):
+        S = _bidiagonal(n, 2, lambda j: lam / (lam + j), lambda j: -lam / (lam + j + 2))
+        exact = _exact(("gegenbauer", lam), ("gegenbauer", lam + 1), n)
+        assert S == exact
+    for a, b in ((Fr(1, 2), Fr(1, 4)), (Fr(-1, 2), Fr(-3, 4)), (Fr(1, 3), Fr(1, 3))):
+        s = a + b
+        diag = lambda j: Fr(1) if j == 0 else (j + s + 1) / (2 * j + s + 1)
+        S = _bidiagonal(n, 1, diag, lambda j: -(j + b + 1) / (2 * j + s + 3))
+        exact = _exact(("jacobi", a, b), ("jacobi", a + 1, b), n)
+        assert S == exact
+        printed = _bidiagonal(n, 1, diag, lambda j: -(j + a + 1) / (2 * j + s + 3))
+        assert (printed == exact) == (a == b)
+        # raising b: the reflection P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x) flips the
+        # superdiagonal's sign
+        Sb = _bidiagonal(n, 1, diag, lambda j: (j + a + 1) / (2 * j + s + 3))
+        assert Sb == _exact(("jacobi", a, b), ("jacobi", a, b + 1), n)
