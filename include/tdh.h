@@ -36,6 +36,8 @@ extern "C" {
 #define TDH_ULTRA2ULTRA 2 /* ultraspherical C^(l1) -> C^(l2), Sec. 5.2, p = {l1, l2}          */
 #define TDH_JAC2JAC     3 /* Jacobi P^(a,b) -> P^(g,d), Sec. 5.3, p = {a, b, g, d}           */
 #define TDH_LAG2LAG     4 /* generalised Laguerre L^(a1) -> L^(a2), Sec. 5.4, p = {a1, a2}   */
+#define TDH_JAC2CHEB    5 /* Jacobi P^(a,b) -> Chebyshev T, Sec. 5.3 (end), p = {a, b}      */
+#define TDH_CHEB2JAC    6 /* Chebyshev T -> Jacobi P^(a,b), Sec. 5.3 (end), p = {a, b}      */
 
 /* ---------------------------------------------------------------- execute precisions */
 #define TDH_FP64  0 /* float64 in/out, float64 FFT                                             */
@@ -58,7 +60,8 @@ extern "C" {
 typedef struct tdh_plan_s* tdh_plan_t; /* opaque; immutable after creation */
 
 typedef struct {
-    double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; LAG {a1, a2}         */
+    double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; LAG {a1, a2};
+                     JAC2CHEB / CHEB2JAC {a, b}                                              */
     int prec;     /* TDH_FP64 or TDH_FP32: the precision of plan_execute's in/out and FFTs  */
     int flags;    /* TDH_FLAG_* (none defined yet; pass 0)                                  */
     int64_t kmax; /* cap on the rank of each Hankel factorisation; 0 selects 128            */
@@ -75,6 +78,23 @@ typedef struct {
  * For TDH_CHEB2LEG the factorisation covers indices 1..n_max-1 and row 0 is applied directly
  * (Sec. 5.1).  tol > 0 is relative to the largest diagonal entry of H; the paper takes
  * "a small multiple of machine epsilon" of the arithmetic used.
+ * Case dispatch (a plan is a chain of steps applied in order):
+ *   ULTRA (l1, l2 > 0): integer l2 - l1 (Case 1): sparse factors S_l of
+ *     eq. (sparseFactorization), or their inverses by back-substitution when l2 < l1;
+ *     |l2 - l1| > 1 not an integer (Case 3): whole steps with those factors until the
+ *     difference is below one, then Case 2 (T o H).  Differences within 1e-14 (relative) of
+ *     an integer count as integers.
+ *   JAC (a, b, g, d > -1): with b != d, first b -> d in the reflected frame
+ *     P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x), then a -> g; each part takes Case 1 / 4 whole
+ *     steps with the bidiagonal factors S_(a,b) (inverses when lowering) and one Case 2
+ *     (T o H) step for a fractional rest, or Case 3 (row 0 direct) when that step's source
+ *     parameters sum to <= -1.  The T o H step runs at the lower end of the range (first
+ *     when raising, last when lowering), where the diagonal scalings amplify the Hankel
+ *     factorisation's rounding least.
+ *   JAC2CHEB / CHEB2JAC: the Jacobi chain to / from (-1/2, -1/2) with the normalisation
+ *     T_k = P_k^(-1/2,-1/2) / P_k^(-1/2,-1/2)(1) folded into its last / first step.
+ *   LAG (a1, a2 > -1): one Toeplitz step (H = all ones).
+ * Parameter differences above 4096 return UNSUPPORTED.
  * Synchronous: returns after the plan is complete.  *out receives the handle.
  * Errors: INVALID_ARG (kind, n_max < 1, tol <= 0, NULL out/params, parameters outside the
  * supported case), UNSUPPORTED (a case this build lacks), NOMEM, CUDA.
@@ -102,7 +122,8 @@ int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, 
  * in, out: device arrays of offsets[batch] values of the plan's precision; out must not
  * overlap in (not checked).  offsets: device, batch + 1 int64, non-decreasing, offsets[0] >= 0.
  * The plan must have been created with TDH_FLAG_RAGGED (else TDH_ERR_INVALID_ARG) and have a
- * single conversion step (Legendre/Chebyshev/ultraspherical Case 2) with FFT lengths within
+ * single T o H conversion step (Legendre/Chebyshev/ultraspherical Case 2; plan creation with
+ * the flag returns UNSUPPORTED for other chains) with FFT lengths within
  * one thread-block cluster.  Vectors are grouped by FFT length on the device; each length
  * class is converted by one persistent launch that takes vectors from a work counter, and the
  * classes run concurrently on plan-owned streams forked from `stream` (capturable in a CUDA

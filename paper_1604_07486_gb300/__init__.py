@@ -11,10 +11,10 @@ import os
 
 from . import build as _build
 
-LEG2CHEB, CHEB2LEG, ULTRA2ULTRA, JAC2JAC, LAG2LAG = 0, 1, 2, 3, 4
+LEG2CHEB, CHEB2LEG, ULTRA2ULTRA, JAC2JAC, LAG2LAG, JAC2CHEB, CHEB2JAC = 0, 1, 2, 3, 4, 5, 6
 FP64, FP32 = 0, 1
 KINDS = {"leg2cheb": LEG2CHEB, "cheb2leg": CHEB2LEG, "ultra2ultra": ULTRA2ULTRA,
-         "jac2jac": JAC2JAC, "lag2lag": LAG2LAG}
+         "jac2jac": JAC2JAC, "lag2lag": LAG2LAG, "jac2cheb": JAC2CHEB, "cheb2jac": CHEB2JAC}
 PRECS = {"fp64": FP64, "fp32": FP32}
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "NOMEM", -4: "ALIGN",
           -5: "TIMEOUT", -6: "CUDA", -7: "ALIAS"}

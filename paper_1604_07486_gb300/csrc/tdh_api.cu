@@ -1,4 +1,5 @@
 // C ABI: plan construction (Fig. 1 steps 1-2), execution (steps 3-5), queries, errors.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -52,7 +53,9 @@ void release_step(Step& st) {
     for (auto& ex : st.rcls) exec_release(ex);
     st.rcls.clear();
     dev_free(st.u_nat);
-    dev_free(st.band_coef);
+    dev_free(st.sp_tab);
+    dev_free(st.scale_out);
+    dev_free(st.scale_in);
     dev_free(st.t);
     dev_free(st.h);
     dev_free(st.d1);
@@ -69,8 +72,8 @@ void release_step(Step& st) {
 // Build one conversion step: symbols (a1), pivoted Cholesky (a2), execute tables (a3).
 int build_step(Step& st, double tol, int64_t kmax, int prec, cudaStream_t s) {
     const int64_t n = st.n;
-    if (st.banded_M > 0)  // sparse factors: only their coefficient table
-        return banded_prepare(prec, n, st.banded_lam0, st.banded_M, &st.band_coef, s);
+    if (st.sp_M > 0)  // sparse factors: only their tables
+        return sparse_prepare(st, prec, s);
     TDH_TRY(dev_alloc_t(&st.t, n));
     TDH_TRY(dev_alloc_t(&st.h, 2 * n - 1));
     TDH_TRY(dev_alloc_t(&st.d1, n));
@@ -146,29 +149,131 @@ int run(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream,
         return TDH_OK;
     }
     // A = A_m ... A_1: the first step reads `in`, later steps work in place on `out` (each
-    // cluster reads its whole vector before writing it); A^T runs the steps in reverse.
+    // cluster reads its whole vector before writing it; sparse factors save their tiles'
+    // halos first); A^T runs the steps in reverse.
     for (size_t i = 0; i < nsteps; ++i) {
         const Step& st = plan->steps[adjoint ? nsteps - 1 - i : i];
-        if (st.banded_M > 0) {
-            // the tiled sparse-factor kernel reads a halo from neighbouring tiles: out of place
-            if (i != 0) {
-                set_error("this chain's transpose would apply sparse factors in place "
-                          "(not built)");
-                return TDH_ERR_UNSUPPORTED;
-            }
-            TDH_TRY(banded_launch(plan->params.prec, in, out, st.n, batch, st.band_coef,
-                                  st.banded_M, adjoint, s));
-            continue;
-        }
-        TDH_TRY(exec_launch(st, plan->params.prec, i == 0 ? in : out, out, batch, adjoint, s));
+        const void* src = i == 0 ? in : out;
+        if (st.sp_M > 0)
+            TDH_TRY(sparse_launch(st, plan->params.prec, src, out, batch, adjoint, s));
+        else
+            TDH_TRY(exec_launch(st, plan->params.prec, src, out, batch, adjoint, s));
     }
     return TDH_OK;
 }
 
-bool case2(double a, double b, double g) {
-    // Sec. 5.3 Case 2 (|a - g| < 1, a != g, a + b > -1) or Case 3 (the same with a + b <= -1)
-    (void)b;
-    return std::fabs(a - g) < 1.0 && a != g;
+// Parameters are usually given in decimal: differences within 1e-14 (relative) of an integer
+// count as integers (Case 1), so e.g. 0.1 -> 1.1 takes one sparse factor.
+bool near_integer(double x) {
+    return std::fabs(x - std::round(x)) <= 1e-14 * std::max(1.0, std::fabs(x));
+}
+
+// Whole steps x -> x +- M with sparse factors, at most kMaxSparse factors per step; returns
+// the parameter reached.
+constexpr int kMaxSparse = 16;
+double sparse_steps(std::vector<Step>& steps, int kind, int64_t n, int family, double x, int M,
+                    int up, double b, int flip) {
+    while (M > 0) {
+        const int m = std::min(M, kMaxSparse);
+        Step st;
+        st.kind = kind;
+        st.n = n;
+        st.sp_M = m;
+        st.sp_family = family;
+        st.sp_off = family == SP_ULTRA ? 2 : 1;
+        st.sp_b = b;
+        st.sp_flip = flip;
+        st.sp_inverse = up ? 0 : 1;
+        // up: S_x, S_{x+1}, ...; down: inverses of S_{x-1}, S_{x-2}, ...
+        st.sp_par0 = up ? x : x - 1.0;
+        st.sp_dir = up ? 1.0 : -1.0;
+        steps.push_back(st);
+        x += up ? m : -m;
+        M -= m;
+    }
+    return x;
+}
+
+// Whole steps while |y - x| >= 1 (Case 1, or the reduction of Case 3 / Case 4), returning the
+// parameter reached; *rest is set when a fractional difference is left for a T o H step.
+double whole_steps(std::vector<Step>& steps, int kind, int64_t n, int family, double x, double y,
+                   double b, int flip, bool* rest) {
+    const double d = y - x;
+    const bool integer = near_integer(d);
+    const int M = integer ? (int)std::lround(std::fabs(d)) : (int)std::floor(std::fabs(d));
+    *rest = !integer;
+    return sparse_steps(steps, kind, n, family, x, M, d > 0, b, flip);
+}
+
+// Whole steps and fractional rest of one parameter's change x -> y.
+struct ParamPath {
+    int M;         // whole steps (Case 1 / Case 4)
+    bool integer;  // no fractional rest (Case 1)
+    bool up;
+};
+
+ParamPath param_path(double x, double y) {
+    const double d = y - x;
+    ParamPath p;
+    p.integer = near_integer(d);
+    p.M = p.integer ? (int)std::lround(std::fabs(d)) : (int)std::floor(std::fabs(d));
+    p.up = d > 0;
+    return p;
+}
+
+// One Case 2 / Case 3 step x -> y of the first Jacobi parameter at fixed second parameter o
+// (reflected: in the frame P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x), i.e. conjugated by
+// diag((-1)^k)).
+void jacobi_toh(std::vector<Step>& steps, int64_t n, double x, double y, double o, int reflected) {
+    Step st;
+    st.kind = TDH_JAC2JAC;
+    st.n = n;
+    st.full = 1;
+    st.sign_in = st.sign_out = reflected;
+    st.p[0] = x;
+    st.p[1] = o;
+    st.p[2] = y;
+    steps.push_back(st);
+}
+
+// Jacobi (a, b) -> (g, d), Sec. 5.3: a changes at fixed b directly, b at fixed a through the
+// reflection.  Each change splits into whole steps with the bidiagonal factors (Case 1 /
+// Case 4; their inverses, by back-substitution, when lowering) and one Toeplitz-dot-Hankel
+// step for a fractional rest (Case 2, or Case 3 when its source parameters sum to <= -1).
+// All conversion matrices compose, so the chain is free to choose the order, and it picks
+// the one with the least error: every downward whole step first, then the T o H steps at
+// the lower end of each range, then every upward whole step.  The paper raises the parameter
+// before the T o H step; at the higher end D1 grows like j^(g+1) and D2 like k^(-a), which
+// amplifies the Hankel factorisation's rounding (measured at n = 5001, (0.25, 0) ->
+// (1.75, 0): 2e-13 relative in the paper's order, 5e-16 in this one), and downward whole
+// steps after a T o H step would sum its rounding errors over the whole tail (measured 1e-2
+// in float32 for Jacobi (1.5, 0.25) -> (-1/2, -1/2)).
+void jacobi_chain(std::vector<Step>& steps, int64_t n, double a, double b, double g, double d) {
+    const ParamPath pa = param_path(a, g), pb = param_path(b, d);
+    // downward whole steps
+    if (!pa.up && pa.M > 0) {
+        a = sparse_steps(steps, TDH_JAC2JAC, n, SP_JACOBI, a, pa.M, 0, b, 0);
+        if (pa.integer) a = g;
+    }
+    if (!pb.up && pb.M > 0) {
+        b = sparse_steps(steps, TDH_JAC2JAC, n, SP_JACOBI, b, pb.M, 0, a, 1);
+        if (pb.integer) b = d;
+    }
+    // fractional rests
+    if (!pb.integer) {
+        const double to = pb.up ? d - pb.M : d;
+        jacobi_toh(steps, n, b, to, a, 1);
+        b = to;
+    }
+    if (!pa.integer) {
+        const double to = pa.up ? g - pa.M : g;
+        jacobi_toh(steps, n, a, to, b, 0);
+        a = to;
+    }
+    // upward whole steps
+    if (pb.up && pb.M > 0) sparse_steps(steps, TDH_JAC2JAC, n, SP_JACOBI, b, pb.M, 1, a, 1);
+    b = d;
+    if (pa.up && pa.M > 0) sparse_steps(steps, TDH_JAC2JAC, n, SP_JACOBI, a, pa.M, 1, b, 0);
 }
 
 }  // namespace
@@ -188,7 +293,7 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         return TDH_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (kind < TDH_LEG2CHEB || kind > TDH_LAG2LAG) {
+    if (kind < TDH_LEG2CHEB || kind > TDH_CHEB2JAC) {
         set_error("unknown kind %d", kind);
         return TDH_ERR_INVALID_ARG;
     }
@@ -204,29 +309,28 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         set_error("kmax must be >= 0");
         return TDH_ERR_INVALID_ARG;
     }
-    if (kind == TDH_JAC2JAC) {
-        const double a = params->p[0], b = params->p[1], g = params->p[2], d = params->p[3];
-        if (!(a > -1.0) || !(b > -1.0) || !(g > -1.0) || !(d > -1.0)) {
-            set_error("Jacobi parameters must be > -1");
+    const double* p = params->p;
+    const int njac = kind == TDH_JAC2JAC ? 4 : (kind == TDH_JAC2CHEB || kind == TDH_CHEB2JAC) ? 2 : 0;
+    for (int i = 0; i < njac; ++i) {
+        if (!(p[i] > -1.0) || !std::isfinite(p[i])) {
+            set_error("Jacobi parameters must be finite and > -1");
             return TDH_ERR_INVALID_ARG;
-        }
-        if ((b != d && !case2(b, a, d)) || (a != g && !case2(a, d, g))) {
-            set_error("Jacobi conversion is built for chains of Case-2/3 steps "
-                      "(|b-d| < 1 and |a-g| < 1); Case 4 (integer shifts) is not built");
-            return TDH_ERR_UNSUPPORTED;
         }
     }
-    if (kind == TDH_ULTRA2ULTRA) {
-        double l1 = params->p[0], l2 = params->p[1];
-        if (!(l1 > 0.0) || !(l2 > 0.0)) {
-            set_error("ultraspherical parameters must be > 0");
-            return TDH_ERR_INVALID_ARG;
-        }
-        if (l1 - l2 >= 1.0) {
-            set_error("ultraspherical conversion to a smaller parameter by 1 or more needs "
-                      "back-substitution (not built)");
-            return TDH_ERR_UNSUPPORTED;
-        }
+    if (kind == TDH_ULTRA2ULTRA && (!(p[0] > 0.0) || !(p[1] > 0.0) || !std::isfinite(p[0]) ||
+                                    !std::isfinite(p[1]))) {
+        set_error("ultraspherical parameters must be finite and > 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (kind == TDH_LAG2LAG && (!(p[0] > -1.0) || !(p[1] > -1.0))) {
+        set_error("Laguerre parameters must be > -1");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if ((kind == TDH_ULTRA2ULTRA && std::fabs(p[1] - p[0]) > 4096.0) ||
+        (kind == TDH_JAC2JAC && (std::fabs(p[2] - p[0]) > 4096.0 || std::fabs(p[3] - p[1]) > 4096.0)) ||
+        ((kind == TDH_JAC2CHEB || kind == TDH_CHEB2JAC) && (p[0] > 4096.0 || p[1] > 4096.0))) {
+        set_error("parameter differences above 4096 are not supported");
+        return TDH_ERR_UNSUPPORTED;
     }
     tdh_plan_s* plan = new (std::nothrow) tdh_plan_s;
     if (!plan) {
@@ -247,73 +351,61 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         delete plan;
         return TDH_ERR_CUDA;
     }
+    std::vector<Step>& steps = plan->steps;
     if (kind == TDH_JAC2JAC) {
-        // Sec. 5.3: with b != d, reflect (P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x)), convert the
-        // first parameter b -> d, reflect back; then convert a -> g at fixed d.
-        const double a = params->p[0], b = params->p[1], g = params->p[2], d = params->p[3];
-        if (b != d) {
+        // Sec. 5.3: Cases 1-4, with the reflection when b != d
+        jacobi_chain(steps, n_max, p[0], p[1], p[2], p[3]);
+    } else if (kind == TDH_JAC2CHEB || kind == TDH_CHEB2JAC) {
+        // T_k = P_k^(-1/2,-1/2) / P_k^(-1/2,-1/2)(1) (Sec. 5.3, end): a Jacobi conversion to or
+        // from (-1/2, -1/2) with the normalisation folded into its last or first step
+        const bool to_cheb = kind == TDH_JAC2CHEB;
+        if (to_cheb)
+            jacobi_chain(steps, n_max, p[0], p[1], -0.5, -0.5);
+        else
+            jacobi_chain(steps, n_max, -0.5, -0.5, p[0], p[1]);
+        if (steps.empty()) {  // (a, b) = (-1/2, -1/2): the normalisation alone
             Step st;
-            st.kind = kind;
+            st.kind = TDH_JAC2JAC;
             st.n = n_max;
-            st.full = 1;
-            st.sign_in = st.sign_out = 1;
-            st.p[0] = b;
-            st.p[1] = a;
-            st.p[2] = d;
-            plan->steps.push_back(st);
+            st.sp_M = 1;
+            st.sp_family = SP_IDENTITY;
+            st.sp_off = 1;
+            steps.push_back(st);
         }
-        if (a != g) {
-            Step st;
-            st.kind = kind;
-            st.n = n_max;
-            st.full = 1;
-            st.p[0] = a;
-            st.p[1] = d;
-            st.p[2] = g;
-            plan->steps.push_back(st);
-        }
+        Step& target = to_cheb ? steps.back() : steps.front();
+        double** slot = to_cheb ? &target.scale_out : &target.scale_in;
+        rc = dev_alloc_t(slot, (size_t)n_max);
+        if (rc == TDH_OK) rc = chebyshev_scale_launch(n_max, to_cheb ? 0 : 1, *slot, s);
     } else if (kind == TDH_ULTRA2ULTRA) {
-        // Sec. 5.2: Case 1 (l2 - l1 a positive integer): sparse factors only; Case 3
-        // (l2 - l1 > 1, not an integer): raise l1 by whole steps with the sparse factors,
-        // then Case 2 (|l1 - l2| < 1) with the Toeplitz-dot-Hankel product.
-        double l1 = params->p[0], l2 = params->p[1];
-        const double up = std::floor(l2 - l1);
-        if (up >= 1.0) {
-            Step st;
-            st.kind = kind;
-            st.n = n_max;
-            st.banded_M = (int)up;
-            st.banded_lam0 = l1;
-            plan->steps.push_back(st);
-            l1 += up;
-        }
-        if (l1 != l2) {
+        // Sec. 5.2: Case 1 (integer difference): sparse factors only; Case 3 (difference above
+        // one, not an integer): whole steps with the sparse factors, then Case 2 (|l1 - l2| < 1)
+        // with the Toeplitz-dot-Hankel product.  Downward steps apply the factors' inverses.
+        bool rest = false;
+        const double l1 = whole_steps(steps, kind, n_max, SP_ULTRA, p[0], p[1], 0.0, 0, &rest);
+        if (rest) {
             Step st;
             st.kind = kind;
             st.n = n_max;
             st.p[0] = l1;
-            st.p[1] = l2;
-            plan->steps.push_back(st);
+            st.p[1] = p[1];
+            steps.push_back(st);
         }
     } else if (kind == TDH_LAG2LAG) {
         // Sec. 5.4: Toeplitz only (H = all ones, rank 1); no parity structure
-        if (!(params->p[0] > -1.0) || !(params->p[1] > -1.0)) {
-            rc = TDH_ERR_INVALID_ARG;
-            set_error("Laguerre parameters must be > -1");
-        } else if (params->p[0] != params->p[1]) {
+        if (p[0] != p[1]) {
             Step st;
             st.kind = kind;
             st.n = n_max;
             st.full = 1;
-            std::memcpy(st.p, params->p, sizeof(st.p));
-            plan->steps.push_back(st);
+            std::memcpy(st.p, p, sizeof(st.p));
+            steps.push_back(st);
         }
     } else {
         Step st;
         st.kind = kind;
         st.n = n_max;
-        std::memcpy(st.p, params->p, sizeof(st.p));
-        plan->steps.push_back(st);
+        std::memcpy(st.p, p, sizeof(st.p));
+        steps.push_back(st);
     }
     for (auto& st : plan->steps) {
         if (rc != TDH_OK) break;

@@ -161,14 +161,23 @@ __global__ void k_cast(const double* __restrict__ in, T* __restrict__ out, int64
     if (i < count) out[i] = (T)in[i];
 }
 
-// row 0 of A = D1 (T o H) D2 (valid for k >= 1), with A_00 = 1 (Sec. 5.1, Sec. 5.3 Case 3)
+// row 0 of A = D1 (T o H) D2 (valid for k >= 1), with A_00 = 1 (Sec. 5.1, Sec. 5.3 Case 3);
+// with the step's scalings A_00 becomes so_0 si_0 (d1, d2 already carry them)
 template <typename T>
 __global__ void k_row0(const double* __restrict__ t, const double* __restrict__ h,
                        const double* __restrict__ d1, const double* __restrict__ d2, int64_t n,
+                       const double* __restrict__ so, const double* __restrict__ si,
                        T* __restrict__ out) {
     int64_t k = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (k >= n) return;
-    out[k] = (k == 0) ? T(1) : (T)(d1[0] * t[k] * h[k] * d2[k]);
+    const double a00 = (so ? so[0] : 1.0) * (si ? si[0] : 1.0);
+    out[k] = (k == 0) ? (T)a00 : (T)(d1[0] * t[k] * h[k] * d2[k]);
+}
+
+// d[i] *= s[i]
+__global__ void k_scale(double* __restrict__ d, const double* __restrict__ s, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < n) d[i] *= s[i];
 }
 
 template <typename T>
@@ -264,13 +273,17 @@ out:
 template <typename T>
 int prepare_diagonals(Step& st, cudaStream_t s) {
     const int64_t n = st.n;
+    // diag(scale_out) D1 (T o H) D2 diag(scale_in)
+    if (st.scale_out) k_scale<<<blocks_for(n), kThreads, 0, s>>>(st.d1, st.scale_out, n);
+    if (st.scale_in) k_scale<<<blocks_for(n), kThreads, 0, s>>>(st.d2, st.scale_in, n);
     TDH_TRY(dev_alloc(&st.d1x, sizeof(T) * n));
     TDH_TRY(dev_alloc(&st.d2x, sizeof(T) * n));
     k_cast<T><<<blocks_for(n), kThreads, 0, s>>>(st.d1, (T*)st.d1x, n);
     k_cast<T><<<blocks_for(n), kThreads, 0, s>>>(st.d2, (T*)st.d2x, n);
     if (st.j0 == 1) {
         TDH_TRY(dev_alloc(&st.row0, sizeof(T) * n));
-        k_row0<T><<<blocks_for(n), kThreads, 0, s>>>(st.t, st.h, st.d1, st.d2, n, (T*)st.row0);
+        k_row0<T><<<blocks_for(n), kThreads, 0, s>>>(st.t, st.h, st.d1, st.d2, n, st.scale_out,
+                                                     st.scale_in, (T*)st.row0);
     }
     TDH_CUDA(cudaGetLastError());
     return TDH_OK;
@@ -396,7 +409,7 @@ int prepare_ragged_typed(Step& st, int prec, cudaStream_t s) {
 }  // namespace
 
 int exec_prepare_ragged(Step& st, int prec, cudaStream_t s) {
-    if (st.full || st.banded_M > 0) {
+    if (st.full || st.sp_M > 0) {
         set_error("ragged batches are built for the parity-packed kinds");
         return TDH_ERR_UNSUPPORTED;
     }

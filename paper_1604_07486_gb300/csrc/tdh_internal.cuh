@@ -93,9 +93,21 @@ struct Step {
     int full = 0;          // Toeplitz part without parity structure (Jacobi): rank-pair packing
     int sign_in = 0;       // (-1)^k on the input (reflection step of a Jacobi chain)
     int sign_out = 0;      // (-1)^k on the output
-    int banded_M = 0;      // > 0: Case-1 step of M sparse factors S_l, no T o H (Sec. 5.2)
-    double banded_lam0 = 0;  // first factor's l
-    void* band_coef = nullptr;  // [M][n+2] l/(l+j) in execute precision
+    // Case-1 step (Sec. 5.2, 5.3): sp_M > 0 sparse factors instead of T o H
+    int sp_M = 0;
+    int sp_family = 0;     // SP_ULTRA (offset 2), SP_JACOBI (offset 1), SP_IDENTITY
+    int sp_off = 0;        // band offset of the factors
+    int sp_inverse = 0;    // apply the factors' inverses (step to a smaller parameter)
+    int sp_flip = 0;       // Jacobi: factors conjugated by diag((-1)^k) (reflected frame)
+    double sp_par0 = 0;    // parameter of the first factor (l, or a of S_(a,b))
+    double sp_dir = 1;     // parameter change from one factor to the next (+1 or -1)
+    double sp_b = 0;       // Jacobi: the fixed parameter b
+    void* sp_tab = nullptr;  // [M][2 or 3][sp_ld] factor tables in execute precision
+    int64_t sp_ld = 0;
+    // diagonal scalings folded into this step: the step computes diag(scale_out) A_step
+    // diag(scale_in) (float64 device arrays of n entries, owned by the step, may be null)
+    double* scale_out = nullptr;
+    double* scale_in = nullptr;
     double* t = nullptr;   // [n]
     double* h = nullptr;   // [2n-1]
     double* d1 = nullptr;  // [n]
@@ -125,11 +137,15 @@ struct tdh_plan_s {
 };
 
 namespace tdh {
-// Case-1 sparse factors: coefficient tables, then out = S_{l0+M-1} ... S_{l0} in (or the
-// transpose); out != in.
-int banded_prepare(int prec, int64_t n, double lam0, int M, void** coef, cudaStream_t s);
-int banded_launch(int prec, const void* in, void* out, int64_t n, int64_t batch, const void* coef,
-                  int M, int adjoint, cudaStream_t s);
+// Case-1 sparse factors: tables of st's factors (scalings folded in), then out = product of
+// the factors (or of their inverses) applied to in, or its transpose; in == out allowed.
+enum { SP_ULTRA = 0, SP_JACOBI = 1, SP_IDENTITY = 2 };
+int sparse_prepare(Step& st, int prec, cudaStream_t s);
+int sparse_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
+                  cudaStream_t s);
+// P_k^(-1/2,-1/2)(1) = Gamma(k+1/2)/(Gamma(1/2) Gamma(k+1)), k < n (its reciprocal if
+// `inverse`), float64 device array: T_k = P_k^(-1/2,-1/2) / P_k^(-1/2,-1/2)(1).
+int chebyshev_scale_launch(int64_t n, int inverse, double* out, cudaStream_t s);
 // Build the execute configuration of `st` for precision `prec` (spectrum, twiddles, factors).
 int exec_prepare(Step& st, int prec, cudaStream_t s);
 void exec_release(ExecData& ex);

@@ -2,14 +2,18 @@
 //
 // Every generator entry is a scaled Gamma ratio Gamma(z + a) / Gamma(z + b) at z on a
 // uniform grid.  Differences of log-gamma values lose about log10(z) digits at large z
-// (the absolute error of lgamma(z) is ~ z log z ulp), so instead:
-//   z >= Z0:  Gamma(z+a)/Gamma(z+b) = z^(a-b) exp(S(1/z)), with S the difference of the two
-//             Stirling series, S = sum_k (-1)^(k+1) [B_{k+1}(a) - B_{k+1}(b)] / (k(k+1) z^k)
+// (the absolute error of lgamma(z) is ~ z log z ulp), so instead the pair is centred,
+// Gamma(z+a)/Gamma(z+b) = Gamma(w+h)/Gamma(w-h) with w = z + (a+b)/2, h = (a-b)/2, and
+//   w >= Zt:  Gamma(w+h)/Gamma(w-h) = w^(2h) exp(S(1/w)), with S the difference of the two
+//             Stirling series, S = sum_k (-1)^(k+1) [B_{k+1}(h) - B_{k+1}(-h)] / (k(k+1) w^k)
 //             (B_k the Bernoulli polynomials; the asymptotic ratio expansion the paper cites
 //             from Tricomi & Erdelyi, used in the proof of Thm 3.2);
-//   z <  Z0:  shift up with Gamma(x + 1) = x Gamma(x) until z >= Z0.
-// With Z0 = 16 and 16 series terms the truncation error is below 1e-20 relative; the result
-// carries the rounding of pow and exp, a few ulp.
+//   w <  Zt:  shift up with Gamma(x + 1) = x Gamma(x) until w >= Zt.
+// The series terms behave like (h/w)^k and k!/(2 pi w)^k: with Zt = 16 + 4|a-b| and 16 terms
+// the truncation error is below 1e-19 relative for any a, b (centring keeps large parameters,
+// e.g. l = 17 in an ultraspherical symbol, out of the series).  The result carries the
+// rounding of pow and exp, a few ulp.  The same routine runs on the host for the constant
+// factors Gamma(x)/Gamma(y) (no overflow of Gamma itself for large x, y).
 #include <cmath>
 #include <cstdarg>
 #include <vector>
@@ -24,6 +28,7 @@ constexpr double kZ0 = 16.0;
 
 struct TableSpec {
     double a, b;         // ratio Gamma(z + a) / Gamma(z + b); ignored when no_ratio
+    double cen, h, zt;   // centre (a+b)/2, half difference (a-b)/2, series threshold
     double z0, dz;       // z = z0 + dz * i
     double scale;        // overall factor
     double lin0, lin1;   // extra factor (lin0 + lin1 * i) when use_lin
@@ -72,11 +77,14 @@ TableSpec ratio_spec(double a, double b, double z0, double dz, double scale) {
     TableSpec s{};
     s.a = a;
     s.b = b;
+    s.cen = 0.5 * (a + b);
+    s.h = 0.5 * (a - b);
+    s.zt = kZ0 + 4.0 * std::fabs(a - b);
     s.z0 = z0;
     s.dz = dz;
     s.scale = scale;
     s.special_i = -1;
-    series_coeffs(a, b, s.c);
+    series_coeffs(s.h, -s.h, s.c);
     return s;
 }
 
@@ -91,24 +99,28 @@ TableSpec linear_spec(double scale, double lin0, double lin1) {
     return s;
 }
 
-__device__ double gamma_ratio(double z, const TableSpec& s) {
+__host__ __device__ double gamma_ratio(double z, const TableSpec& s) {
+    double w = z + s.cen;
     double f = 1.0;
-    if (z < kZ0) {
-        int N = (int)ceil(kZ0 - z);
+    if (w < s.zt) {
+        const int N = (int)ceil(s.zt - w);
         double num = 1.0, den = 1.0;
         for (int i = 0; i < N; ++i) {
-            num *= (z + s.b + (double)i);
-            den *= (z + s.a + (double)i);
+            num *= (w - s.h + (double)i);  // = z + b + i
+            den *= (w + s.h + (double)i);  // = z + a + i
         }
         f = num / den;
-        z += (double)N;
+        w += (double)N;
     }
-    double iz = 1.0 / z;
+    const double iw = 1.0 / w;
     double S = 0.0;
 #pragma unroll
-    for (int k = kTerms; k >= 1; --k) S = (S + s.c[k - 1]) * iz;
-    return f * pow(z, s.a - s.b) * exp(S);
+    for (int k = kTerms; k >= 1; --k) S = (S + s.c[k - 1]) * iw;
+    return f * pow(w, 2.0 * s.h) * exp(S);
 }
+
+// Gamma(x) / Gamma(y) on the host (x, y not at poles).
+double gratio(double x, double y) { return gamma_ratio(0.0, ratio_spec(x, y, 0.0, 1.0, 1.0)); }
 
 __global__ void table_kernel(TableSpec s, int64_t count, double* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -138,6 +150,14 @@ int launch_table(const TableSpec& s, int64_t count, double* out, cudaStream_t st
 bool is_nonpos_integer(double x) { return x <= 0.0 && std::floor(x) == x; }
 
 }  // namespace
+
+int chebyshev_scale_launch(int64_t n, int inverse, double* out, cudaStream_t st) {
+    // Gamma(k + 1/2) / (Gamma(1/2) Gamma(k + 1)), or its reciprocal
+    const double sqrtpi = 1.7724538509055160273;
+    const TableSpec ts = inverse ? ratio_spec(1.0, 0.5, 0.0, 1.0, sqrtpi)
+                                 : ratio_spec(0.5, 1.0, 0.0, 1.0, 1.0 / sqrtpi);
+    return launch_table(ts, n, out, st);
+}
 
 int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, double* d1,
                    double* d2, cudaStream_t st) {
@@ -192,7 +212,7 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
         TableSpec ts = ratio_spec(d, 1.0, 0.0, 0.5, 1.0 / std::tgamma(d));
         ts.even_only = 1;
         TDH_TRY(launch_table(ts, n, t, st));
-        TDH_TRY(launch_table(ratio_spec(l1, l2 + 1.0, 0.0, 0.5, std::tgamma(l2) / std::tgamma(l1)),
+        TDH_TRY(launch_table(ratio_spec(l1, l2 + 1.0, 0.0, 0.5, gratio(l2, l1)),
                              nh, h, st));
         TDH_TRY(launch_table(linear_spec(1.0, l2, 1.0), n, d1, st));
         TDH_TRY(launch_table(linear_spec(1.0, 1.0, 0.0), n, d2, st));
@@ -222,12 +242,12 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
             // Gamma(s+1)/Gamma(b+1) * Gamma(b+2)/Gamma(s+2) = (b+1)/(s+1), carried by D1.
             // Index-0 entries of h and d2 are unused and set to 0.
             TableSpec hs = ratio_spec(a + b + 1.0, s + 1.0, 0.0, 1.0,
-                                      std::tgamma(s + 2.0) / std::tgamma(a + b + 2.0));
+                                      gratio(s + 2.0, a + b + 2.0));
             hs.special_i = 0;
             hs.special_v = 0.0;
             TDH_TRY(launch_table(hs, nh, h, st));
             TableSpec e1 = ratio_spec(s, b + 1.0, 0.0, 1.0,
-                                      (b + 1.0) / (s + 1.0) * std::tgamma(b + 1.0) / std::tgamma(s + 1.0));
+                                      (b + 1.0) / (s + 1.0) * gratio(b + 1.0, s + 1.0));
             e1.use_lin = 1;
             e1.lin0 = s;
             e1.lin1 = 2.0;
@@ -235,16 +255,16 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
             e1.special_v = (b + 1.0) / (s + 1.0);
             TDH_TRY(launch_table(e1, n, d1, st));
             TableSpec e2 = ratio_spec(b + 1.0, a + b + 1.0, 0.0, 1.0,
-                                      std::tgamma(a + b + 2.0) / std::tgamma(b + 2.0));
+                                      gratio(a + b + 2.0, b + 2.0));
             e2.special_i = 0;
             e2.special_v = 0.0;
             TDH_TRY(launch_table(e2, n, d2, st));
             return TDH_OK;
         }
         TDH_TRY(launch_table(ratio_spec(a + b + 1.0, s + 1.0, 0.0, 1.0,
-                                        std::tgamma(s + 1.0) / std::tgamma(a + b + 1.0)),
+                                        gratio(s + 1.0, a + b + 1.0)),
                              nh, h, st));
-        TableSpec e1 = ratio_spec(s, b + 1.0, 0.0, 1.0, std::tgamma(b + 1.0) / std::tgamma(s + 1.0));
+        TableSpec e1 = ratio_spec(s, b + 1.0, 0.0, 1.0, gratio(b + 1.0, s + 1.0));
         e1.use_lin = 1;
         e1.lin0 = s;
         e1.lin1 = 2.0;
@@ -252,7 +272,7 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
         e1.special_v = 1.0;
         TDH_TRY(launch_table(e1, n, d1, st));
         TDH_TRY(launch_table(ratio_spec(b + 1.0, a + b + 1.0, 0.0, 1.0,
-                                        std::tgamma(a + b + 1.0) / std::tgamma(b + 1.0)),
+                                        gratio(a + b + 1.0, b + 1.0)),
                              n, d2, st));
         return TDH_OK;
     }

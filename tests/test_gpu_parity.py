@@ -201,10 +201,14 @@ def test_error_paths(tdh):
     assert rc == -7
     assert tdh.lib().tdh_plan_execute(plan._h, ctypes.c_void_p(buf.data_ptr()),
                                       ctypes.c_void_p(buf.data_ptr() + 1024), 0, None) == 0
-    with pytest.raises(tdh.TdhError):
-        tdh.Plan("jac2jac", 100, params=(0.1, 0.0, 1.6, 0.0))  # Case 4: not built
+    with pytest.raises(tdh.TdhError) as e:
+        tdh.Plan("jac2jac", 100, params=(-1.0, 0.0, 1.6, 0.0))  # a <= -1
+    assert e.value.code == -1
     with pytest.raises(tdh.TdhError):
         tdh.Plan("ultra2ultra", 100, params=(-1.0, 0.5))
+    with pytest.raises(tdh.TdhError) as e:  # ragged batches need one T o H step
+        tdh.Plan("ultra2ultra", 100, params=(0.25, 1.25), ragged=True)
+    assert e.value.code == -2
     y = plan.execute(x)
     torch.cuda.synchronize()
     assert torch.all(y == 0)
@@ -295,14 +299,6 @@ def test_config4_ultraspherical_n2p20_b16(tdh, prec):
     ref = oracle.matvec(oracle.ULTRA, (0.25, 1.25), alpha, rows=rows)
     err = (np.abs(y[:, rows] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
     assert err <= TOL[prec]
-
-
-def test_jacobi_case4_reported_unsupported(tdh):
-    """|a - g| > 1 (Case 4: integer shifts first) is not built: a clear error, no result."""
-    for params in [(0.1, 0.0, 1.6, 0.0), (0.1, 0.0, -0.95, 0.0)]:
-        with pytest.raises(tdh.TdhError) as e:
-            tdh.Plan("jac2jac", 100, params=params)
-        assert e.value.code == -2
 
 
 # ---------------------------------------------------------------- multi-pass (large L)
