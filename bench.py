@@ -373,7 +373,9 @@ def main():
             "fp64": fp64,
             "e2e": {"value": e2e_value, "unit": "coeffs/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
-            "gpu_launches": len(KINDS) * args.steps,
+            # per direction: the execute kernel and the balanced-split fix-up (36 resident
+            # 4-CTA clusters do not divide 256 x K rank units evenly)
+            "gpu_launches": 2 * len(KINDS) * args.steps,
             "kernel_ms": {"leg2cheb": statistics.mean(t_l2c), "cheb2leg": statistics.mean(t_c2l)},
             "wall_s": wall,
             "clocks": clocks,

@@ -296,17 +296,6 @@ int dispatch(const Geometry& g, const ExecParams<T>& P, int64_t batch, cudaStrea
     return P.ragged ? dispatch_ragged(g, P, batch, s) : dispatch_dense(g, P, batch, s);
 }
 
-// out[v][k] = sum_s partial[s][v][k], fixed order (deterministic)
-template <typename T>
-__global__ void k_split_reduce(const T* __restrict__ partial, T* __restrict__ out, int64_t total,
-                               int nsplit) {
-    int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= total) return;
-    T acc = partial[i];
-    for (int s = 1; s < nsplit; ++s) acc += partial[(int64_t)s * total + i];
-    out[i] = acc;
-}
-
 template <typename T>
 int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int adjoint,
                  cudaStream_t s) {
@@ -338,29 +327,7 @@ int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int a
     P.next = nullptr;
     P.batch = batch;
     P.partial = nullptr;
-    // A batch too small to fill the GPU: split the rank terms over several clusters per vector
-    // and add the partial results in a second pass.
-    const int64_t clusters = batch * ex.g.C;
-    int64_t nsplit = 1;
-    if (P.K > 1 && 2 * clusters < sm_count())
-        nsplit = std::min<int64_t>(std::min<int64_t>(P.K, 32), sm_count() / clusters);
-    P.nsplit = (int)nsplit;
-    if (nsplit <= 1) return dispatch<T>(ex.g, P, batch, s);
-    const int64_t total = batch * st.n;
-    T* partial = nullptr;
-    TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&partial), sizeof(T) * total * nsplit, s));
-    P.partial = partial;
-    int rc = dispatch<T>(ex.g, P, batch * nsplit, s);
-    if (rc == TDH_OK) {
-        k_split_reduce<T><<<blocks_for(total), kThreads, 0, s>>>(partial, P.out, total, (int)nsplit);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) {
-            set_error("split reduce: %s", cudaGetErrorString(e));
-            rc = TDH_ERR_CUDA;
-        }
-    }
-    cudaFreeAsync(partial, s);
-    return rc;
+    return dispatch<T>(ex.g, P, batch, s);
 }
 
 }  // namespace
@@ -495,7 +462,6 @@ int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t
         P.sign_in = 0;
         P.sign_out = 0;
         P.u_stride = ex.u_stride;
-        P.nsplit = 1;
         P.batch = batch;
         P.partial = nullptr;
         P.ragged = 1;

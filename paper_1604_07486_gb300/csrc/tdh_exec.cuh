@@ -90,9 +90,10 @@ struct ExecParams {
     int sign_in;    // multiply input coefficient k by (-1)^k (Jacobi reflection)
     int sign_out;   // multiply output coefficient k by (-1)^k
     int64_t u_stride;  // complex entries between consecutive (rank, k1) rows of u
-    // rank split (small dense batches): cluster (s, v) applies rank terms
-    // [K s / nsplit, K (s+1) / nsplit) of vector v and writes partial[s][v][*]
-    int nsplit;
+    // dense batches, balanced split: the launch's G clusters share the batch's U = batch * Ku
+    // (vector, rank term) units equally (Ku = max(K, 1)); cluster c applies units
+    // [U c / G, U (c+1) / G) and writes a vector split between clusters as partial sums:
+    // slot 2c+1 for its piece holding rank 0, slot 2c for a later piece (partial: [2G][n])
     int64_t batch;
     T* partial;
     // ragged batches: vector v occupies [offs[v], offs[v+1]); this launch converts the
@@ -525,18 +526,22 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
     if constexpr (C > 1) k1 = (int)cg::this_cluster().block_rank();
     for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
     if constexpr (!RAGGED) {
+        const int64_t G = gridDim.x / C;
         const int64_t cid = blockIdx.x / C;
-        const int64_t vec = cid % P.batch;
-        const int64_t sp = cid / P.batch;
-        T* outp = P.out + vec * P.n;
-        int64_t r0 = 0, r1 = P.K;
-        if (P.nsplit > 1) {
-            r0 = P.K * sp / P.nsplit;
-            r1 = P.K * (sp + 1) / P.nsplit;
-            outp = P.partial + (sp * P.batch + vec) * P.n;
+        const int64_t Ku = P.K > 0 ? P.K : 1;
+        const int64_t U = P.batch * Ku;
+        int64_t u = U * cid / G;
+        const int64_t u1 = U * (cid + 1) / G;
+        for (int it = 0; u < u1; ++it) {
+            if (it > 0) __syncthreads();
+            const int64_t vec = u / Ku, r0 = u % Ku;
+            const int64_t r1 = r0 + u1 - u < Ku ? r0 + u1 - u : Ku;
+            T* outp = (r0 == 0 && r1 == Ku) ? P.out + vec * P.n
+                                            : P.partial + (2 * cid + (r0 == 0 ? 1 : 0)) * P.n;
+            convert_vector<T, LOGLC, R, C, NT>(P, P.in + vec * P.n, outp, P.n, k1, buf, vbuf, twt,
+                                               red, r0, r1 < P.K ? r1 : P.K, r0 == 0);
+            u += r1 - r0;
         }
-        convert_vector<T, LOGLC, R, C, NT>(P, P.in + vec * P.n, outp, P.n, k1, buf, vbuf, twt,
-                                           red, r0, r1, sp == 0);
     } else {
         __shared__ int slot[2];
         const int count = *P.count;
@@ -562,8 +567,26 @@ __global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
     }
 }
 
+// Balanced split, second pass: each vector split between clusters is the sum of its pieces
+// in cluster order (deterministic).  blockIdx.y + 1 = c indexes the boundary between clusters
+// c-1 and c; the first boundary inside a vector owns it.
+template <typename T>
+__global__ void k_balance_fixup(const T* __restrict__ partial, T* __restrict__ out, int64_t n,
+                                int64_t U, int64_t Ku, int64_t G) {
+    const int64_t c = (int64_t)blockIdx.y + 1;
+    const int64_t b = U * c / G;
+    if (b % Ku == 0) return;
+    const int64_t v = b / Ku;
+    if (U * (c - 1) / G > v * Ku) return;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    T acc = partial[(2 * (c - 1) + 1) * n + k];
+    for (int64_t cc = c; cc < G && U * cc / G < (v + 1) * Ku; ++cc) acc += partial[2 * cc * n + k];
+    out[v * n + k] = acc;
+}
+
 template <typename T, int LOGLC, int R, int C, int NT, bool RAGGED>
-int launch_inst(const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
+int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
     constexpr size_t smem = (size_t)(padded_len<V>(G.LC()) + G.LC() / 2 + G.twp_len()) * sizeof(V);
@@ -592,21 +615,58 @@ int launch_inst(const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    if constexpr (RAGGED) {
-        // persistent: as many clusters as can be resident, at most one per vector
-        int resident = 0;
+    // persistent: as many clusters as can be resident (queried once per kernel)
+    static std::once_flag once_res;
+    static int resident = 0;
+    static cudaError_t res_err = cudaSuccess;
+    std::call_once(once_res, [&] {
         if (C > 1) {
-            TDH_CUDA(cudaOccupancyMaxActiveClusters(&resident, kern, &cfg));
+            res_err = cudaOccupancyMaxActiveClusters(&resident, kern, &cfg);
         } else {
             int per_sm = 0;
-            TDH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+            res_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
             resident = per_sm * sm_count();
         }
+    });
+    if (res_err != cudaSuccess) {
+        set_error("occupancy query: %s", cudaGetErrorString(res_err));
+        return TDH_ERR_CUDA;
+    }
+    ExecParams<T> P = P0;
+    if constexpr (RAGGED) {
+        // at most one cluster per vector; vectors come from the class's work counter
         const int64_t nclusters = std::max<int64_t>(1, std::min<int64_t>(batch, resident));
         cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
+        TDH_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
+        return TDH_OK;
+    } else {
+        // balanced split: one wave of G clusters, at most one per (vector, rank term) unit
+        const int64_t Ku = P.K > 0 ? P.K : 1;
+        const int64_t U = batch * Ku;
+        const int64_t G = std::max<int64_t>(1, std::min<int64_t>(U, resident));
+        bool split = false;
+        for (int64_t c = 1; c < G && !split; ++c) split = (U * c / G) % Ku != 0;
+        P.batch = batch;
+        P.partial = nullptr;
+        if (split) {
+            if (G - 1 > 65535) {
+                set_error("balanced split: too many clusters");
+                return TDH_ERR_UNSUPPORTED;
+            }
+            TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&P.partial),
+                                     sizeof(T) * (size_t)(2 * G) * (size_t)P.n, s));
+        }
+        cfg.gridDim = dim3((unsigned)(G * C), 1, 1);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, kern, P);
+        if (e == cudaSuccess && split) {
+            dim3 fg((unsigned)((P.n + 255) / 256), (unsigned)(G - 1), 1);
+            k_balance_fixup<T><<<fg, 256, 0, s>>>(P.partial, P.out, P.n, U, Ku, G);
+            e = cudaGetLastError();
+        }
+        if (P.partial) cudaFreeAsync(P.partial, s);
+        TDH_CUDA(e);
+        return TDH_OK;
     }
-    TDH_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
-    return TDH_OK;
 }
 
 // Kernel instantiation for a geometry (switch over the built configurations).
