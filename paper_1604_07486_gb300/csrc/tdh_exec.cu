@@ -75,16 +75,17 @@ __global__ void k_stockham(const double2* __restrict__ x, double2* __restrict__ 
     y[2 * j * m + k + m] = make_double2(a.x - b.x, a.y - b.y);
 }
 
-// spec[pos][f2] = conj(S[f1(pos) + LC f2]) / L
+// conj(S[f1(pos) + LC f2]) / L at spec[pos][f2] (cluster kernels) or spec[f2][pos]
+// (multi-pass cross stage, `by_f2`)
 template <typename V>
 __global__ void k_spec(const double2* __restrict__ S, const int* __restrict__ perm, int LC, int C,
-                       int64_t L, V* __restrict__ spec) {
+                       int64_t L, int by_f2, V* __restrict__ spec) {
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= (int64_t)LC * C) return;
     const int pos = (int)(i / C), f2 = (int)(i % C);
     const double2 z = S[perm[pos] + (int64_t)LC * f2];
     const double inv = 1.0 / (double)L;
-    spec[i] = from_d2<V>(make_double2(z.x * inv, -z.y * inv));
+    spec[by_f2 ? (int64_t)f2 * LC + pos : i] = from_d2<V>(make_double2(z.x * inv, -z.y * inv));
 }
 
 // twx[pos] = omega_L^{f1(pos)}
@@ -234,7 +235,7 @@ int prepare_typed(Step& st, ExecData& ex, const Geometry& g, const void* shared_
             std::swap(x, y);
         }
         k_spec<V><<<blocks_for((int64_t)LC * C), kThreads, 0, s>>>(x, perm_d, LC, C, L,
-                                                                   (V*)ex.spec);
+                                                                   ex.multipass, (V*)ex.spec);
         if (C > 1 && !ex.multipass)
             k_twx<V><<<blocks_for(LC), kThreads, 0, s>>>(perm_d, LC, L, (V*)ex.twx);
         if (ex.multipass) {

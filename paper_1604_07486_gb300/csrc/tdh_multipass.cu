@@ -5,9 +5,9 @@
 // Per vector b and local slice k1 (z[k1 + C k2], k2 < LC), per rank term r:
 //   mp_fwd   : u_r o v (v staged once in global memory), forward local DIF passes in
 //              shared memory, local spectrum -> Y[b][k1][pos]
-//   mp_cross : for every local position pos, the C values Y[b][*][pos]: twiddle
+//   cross    : for every local position pos, the C values Y[b][*][pos]: twiddle
 //              omega_L^{k1 f1(pos)}, C-point DFT, multiply by conj(S)/L, inverse C-point
-//              DFT, conjugate twiddle (one warp per position, radix-2 in shared memory)
+//              DFT, conjugate twiddle (radix 16 x C/16 in registers for 16 <= C <= 256)
 //   mp_inv   : inverse local DIT passes, W[b][k1][k2] += u_r o y
 // then beta = D1 W (D2 for the adjoint).  Scratch (v, Y, W) is stream-ordered
 // (cudaMallocAsync) and vectors are processed in chunks that bound it.
@@ -210,7 +210,8 @@ __global__ void __launch_bounds__(NT, 1) mp_inv(const MPParams<T> P, int64_t r) 
     }
 }
 
-// Cross stage: one warp per local position, C values in shared memory (padded rows).
+// Cross stage for C outside [16, 256]: one warp per local position, C values in shared memory
+// (padded rows), radix 2.
 template <typename T, int LC>
 __global__ void __launch_bounds__(256) mp_cross(const MPParams<T> P) {
     using V = typename cx<T>::t;
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(256) mp_cross(const MPParams<T> P) {
         const int64_t pos = pos0 + p;
         for (int i = lane; i < C; i += 32) {
             const int f2 = (int)(__brev((unsigned)i) >> (32 - P.logC));
-            const V s = P.spec[pos * C + f2];
+            const V s = P.spec[(int64_t)f2 * LC + pos];
             x[i] = P.adjoint ? cmulc(x[i], s) : cmul(x[i], s);
         }
         __syncwarp();
@@ -267,6 +268,117 @@ __global__ void __launch_bounds__(256) mp_cross(const MPParams<T> P) {
         const int pos = pos0 + p;
         const V w = omega_L(P.thi, P.tlo, (int64_t)k1 * P.perm[pos], P.L, P.shift);
         Yw[(int64_t)k1 * LC + pos] = cmulc(tile[p * ld + k1], w);
+    }
+}
+
+// Cross stage for 16 <= C <= 256 slices: the C-point DFT of each local position split as
+// C = 16 C2 (Cooley-Tukey: k1 = a + C2 b, f = c + 16 d,
+//   X[c + 16 d] = sum_a omega_C2^{a d} omega_C^{a c} sum_b omega_16^{b c} x[a + C2 b]),
+// each short DFT in registers, PP = 4096 / C positions of a block in shared memory
+// ([PP][C + 1]: every phase reads with consecutive positions on consecutive lanes, so the
+// padded rows give conflict-free banks and the global accesses are coalesced).  Then the
+// spectrum (stored [f][pos]) and the inverse in the reverse order.
+template <typename T, int LC, int C>
+__global__ void __launch_bounds__(256) mp_cross16(const MPParams<T> P) {
+    using V = typename cx<T>::t;
+    constexpr int NTH = 256, PP = 4096 / C, C2 = C / 16, LD = C + 1;
+    static_assert(C >= 16 && C <= 256 && LC % PP == 0 && PP * C2 == NTH, "cross-stage shape");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* tile = reinterpret_cast<V*>(smem_raw);  // [PP][LD]
+    V* twc = tile + PP * LD;                   // omega_C^k, k < C
+    const int tid = threadIdx.x;
+    const int64_t bl = blockIdx.y;
+    const int pos0 = blockIdx.x * PP;
+    for (int k = tid; k < C; k += NTH)
+        twc[k] = omega_L(P.thi, P.tlo, (int64_t)k * (P.L / C), P.L, P.shift);
+    V* Yb = P.Y + bl * (int64_t)C * LC;
+    for (int idx = tid; idx < PP * C; idx += NTH) {
+        const int p = idx % PP, k1 = idx / PP;
+        const int pos = pos0 + p;
+        const V w = omega_L(P.thi, P.tlo, (int64_t)k1 * P.perm[pos], P.L, P.shift);
+        tile[p * LD + k1] = cmul(Yb[(int64_t)k1 * LC + pos], w);
+    }
+    __syncthreads();
+    const int pB = tid % PP, aB = tid / PP;  // phases B and D: one (position, a) per thread
+    {
+        V x[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) x[b] = tile[pB * LD + aB + C2 * b];
+        dif<16>(x);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int c = bitrev(jj, 16);
+            tile[pB * LD + aB + C2 * c] = (aB * c == 0) ? x[jj] : cmul(x[jj], twc[aB * c]);
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int g = tid; g < PP * 16; g += NTH) {
+        const int p = g % PP, c = g / PP;
+        const int64_t pos = pos0 + p;
+        V x[C2];
+#pragma unroll
+        for (int a = 0; a < C2; ++a) x[a] = tile[p * LD + a + C2 * c];
+        dif<C2>(x);
+#pragma unroll
+        for (int jj = 0; jj < C2; ++jj) {
+            const V sv = P.spec[(int64_t)(c + 16 * bitrev(jj, C2)) * LC + pos];
+            x[jj] = P.adjoint ? cmulc(x[jj], sv) : cmul(x[jj], sv);
+        }
+        dit<C2>(x);
+#pragma unroll
+        for (int a = 0; a < C2; ++a)
+            tile[p * LD + a + C2 * c] = (a * c == 0) ? x[a] : cmulc(x[a], twc[a * c]);
+    }
+    __syncthreads();
+    {
+        V x[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) x[jj] = tile[pB * LD + aB + C2 * bitrev(jj, 16)];
+        dit<16>(x);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) tile[pB * LD + aB + C2 * b] = x[b];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < PP * C; idx += NTH) {
+        const int p = idx % PP, k1 = idx / PP;
+        const int pos = pos0 + p;
+        const V w = omega_L(P.thi, P.tlo, (int64_t)k1 * P.perm[pos], P.L, P.shift);
+        Yb[(int64_t)k1 * LC + pos] = cmulc(tile[p * LD + k1], w);
+    }
+}
+
+template <typename T, int LC, int C>
+int cross16_launch(const MPParams<T>& Q, int64_t nb, cudaStream_t s) {
+    using V = typename cx<T>::t;
+    constexpr int PP = 4096 / C;
+    constexpr size_t smem = (size_t)(PP * (C + 1) + C) * sizeof(V);
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [&] {
+        err = cudaFuncSetAttribute(mp_cross16<T, LC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+    });
+    if (err != cudaSuccess) {
+        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(err));
+        return TDH_ERR_CUDA;
+    }
+    mp_cross16<T, LC, C><<<dim3(LC / PP, (unsigned)nb), 256, smem, s>>>(Q);
+    return TDH_OK;
+}
+
+// The cross stage for one rank term of a chunk of nb vectors.
+template <typename T, int LC>
+int cross_launch(const MPParams<T>& Q, int64_t nb, size_t smem_cross, cudaStream_t s) {
+    switch (Q.C) {
+    case 16: return cross16_launch<T, LC, 16>(Q, nb, s);
+    case 32: return cross16_launch<T, LC, 32>(Q, nb, s);
+    case 64: return cross16_launch<T, LC, 64>(Q, nb, s);
+    case 128: return cross16_launch<T, LC, 128>(Q, nb, s);
+    case 256: return cross16_launch<T, LC, 256>(Q, nb, s);
+    default:
+        mp_cross<T, LC><<<dim3(LC / 16, (unsigned)nb), 256, smem_cross, s>>>(Q);
+        return TDH_OK;
     }
 }
 
@@ -365,11 +477,12 @@ int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjo
         const unsigned ew = (unsigned)std::min<int64_t>((nb * P.L / 2 + kEw - 1) / kEw, 4096);
         mp_load<T, LC><<<ew, kEw, 0, s>>>(Q, 0, nb);
         if (P.row0) mp_row0<T><<<(unsigned)nb, kEw, 0, s>>>(Q, 0);
-        for (int64_t r = 0; r < P.K; ++r) {
+        for (int64_t r = 0; rc == TDH_OK && r < P.K; ++r) {
             mp_fwd<T, LOGLC, R, NT><<<(unsigned)(nb * P.C), NT, smem_pass, s>>>(Q, r);
-            mp_cross<T, LC><<<dim3(LC / 16, (unsigned)nb), 256, smem_cross, s>>>(Q);
+            rc = cross_launch<T, LC>(Q, nb, smem_cross, s);
             mp_inv<T, LOGLC, R, NT><<<(unsigned)(nb * P.C), NT, smem_pass, s>>>(Q, r);
         }
+        if (rc != TDH_OK) break;
         Q.in = P.in;
         const unsigned eo = (unsigned)std::min<int64_t>((nb * P.n + kEw - 1) / kEw, 4096);
         mp_store<T, LC><<<eo, kEw, 0, s>>>(Q, b0, nb);
