@@ -168,7 +168,15 @@ __global__ void __launch_bounds__(NT, 1) mp_inv(const MPParams<T> P, int64_t r) 
     const int k1 = blockIdx.x % P.C;
     for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
     const V* y = P.Y + (bl * P.C + k1) * LC;
-    for (int pos = tid; pos < LC; pos += NT) buf[sidx<V>(pos)] = y[pos];
+    static_assert(LC % (8 * NT) == 0, "load batches");
+#pragma unroll 1
+    for (int pos0 = tid; pos0 < LC; pos0 += 8 * NT) {
+        V v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = y[pos0 + i * NT];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) buf[sidx<V>(pos0 + i * NT)] = v[i];
+    }
     __syncthreads();
 #pragma unroll 1
     for (int g = tid; g < LC / RL; g += NT) {
@@ -292,14 +300,23 @@ __global__ void __launch_bounds__(256) mp_cross16(const MPParams<T> P) {
     for (int k = tid; k < C; k += NTH)
         twc[k] = omega_L(P.thi, P.tlo, (int64_t)k * (P.L / C), P.L, P.shift);
     V* Yb = P.Y + bl * (int64_t)C * LC;
-    for (int idx = tid; idx < PP * C; idx += NTH) {
-        const int p = idx % PP, k1 = idx / PP;
-        const int pos = pos0 + p;
-        const V w = omega_L(P.thi, P.tlo, (int64_t)k1 * P.perm[pos], P.L, P.shift);
-        tile[p * LD + k1] = cmul(Yb[(int64_t)k1 * LC + pos], w);
+    // phases A and E: thread (p, k0) moves slices k1 = k0 + C2 i, i < 16, of position p (all
+    // loads of a thread independent, so they are in flight together)
+    const int pB = tid % PP, aB = tid / PP;
+    const int64_t fpos = P.perm[pos0 + pB];
+    {
+        V y[16], w[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int k1 = aB + C2 * i;
+            y[i] = Yb[(int64_t)k1 * LC + pos0 + pB];
+            w[i] = omega_L(P.thi, P.tlo, (int64_t)k1 * fpos, P.L, P.shift);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) tile[pB * LD + aB + C2 * i] = cmul(y[i], w[i]);
     }
     __syncthreads();
-    const int pB = tid % PP, aB = tid / PP;  // phases B and D: one (position, a) per thread
+    // phases B and D: one (position, a) per thread
     {
         V x[16];
 #pragma unroll
@@ -340,11 +357,16 @@ __global__ void __launch_bounds__(256) mp_cross16(const MPParams<T> P) {
         for (int b = 0; b < 16; ++b) tile[pB * LD + aB + C2 * b] = x[b];
     }
     __syncthreads();
-    for (int idx = tid; idx < PP * C; idx += NTH) {
-        const int p = idx % PP, k1 = idx / PP;
-        const int pos = pos0 + p;
-        const V w = omega_L(P.thi, P.tlo, (int64_t)k1 * P.perm[pos], P.L, P.shift);
-        Yb[(int64_t)k1 * LC + pos] = cmulc(tile[p * LD + k1], w);
+    {
+        V w[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            w[i] = omega_L(P.thi, P.tlo, (int64_t)(aB + C2 * i) * fpos, P.L, P.shift);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int k1 = aB + C2 * i;
+            Yb[(int64_t)k1 * LC + pos0 + pB] = cmulc(tile[pB * LD + k1], w[i]);
+        }
     }
 }
 
