@@ -263,6 +263,7 @@ def main():
     sampler = ClockSampler(local)
     with sampler:
         barrier()
+        launches0 = tdh.launch_count()
         wall0 = time.perf_counter()
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
@@ -273,6 +274,7 @@ def main():
             ev[i][2].record(stream)
         barrier()
         wall = time.perf_counter() - wall0
+        launches = tdh.launch_count() - launches0
     t_l2c = [e[0].elapsed_time(e[1]) for e in ev]
     t_c2l = [e[1].elapsed_time(e[2]) for e in ev]
     step_ms = [a + b for a, b in zip(t_l2c, t_c2l)]
@@ -374,8 +376,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": "coeffs/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
             # per direction: the execute kernel and the balanced-split fix-up (36 resident
-            # 4-CTA clusters do not divide 256 x K rank units evenly)
-            "gpu_launches": 2 * len(KINDS) * args.steps,
+            # 4-CTA clusters do not divide 256 x K rank units evenly), counted by the library
+            "gpu_launches": launches,
+            "gpu_launches_source": "tdh_launch_count over the timed region",
             "kernel_ms": {"leg2cheb": statistics.mean(t_l2c), "cheb2leg": statistics.mean(t_c2l)},
             "wall_s": wall,
             "clocks": clocks,
@@ -415,7 +418,7 @@ def run_extra(args, rank, world, local):
         x = torch.tensor(alpha, dtype=torch.float64, device="cuda")
         y = torch.empty_like(x)
         fn = lambda: plan.execute(x, out=y)
-        coeffs, dtype, launches = n * B, "f64", 1
+        coeffs, dtype = n * B, "f64"
         flops = flops_per_vector(plan.K, 1024) * B
         bound, peak, unit, pnote = "alu", 1.25, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s (GB300 table)"
         config = {"workload": "leg2cheb n=1024 batch=1 fp64 tol=1e-15", "K": plan.K}
@@ -437,13 +440,14 @@ def run_extra(args, rank, world, local):
             plan.execute_ragged(xt, ot, out=yt)
         stream.wait_stream(side)
         graph = torch.cuda.CUDAGraph()
+        c0 = tdh.launch_count()
         with torch.cuda.graph(graph):
             plan.execute_ragged(xt, ot, out=yt)
+        graph_launches = tdh.launch_count() - c0  # kernels in the captured graph
         fn = graph.replay
         coeffs, dtype = int(offs[-1]), "f32"
         Ls = [max(256, 1 << int(math.ceil(math.log2(max(2 * ((int(n) + 1) // 2) - 1, 1))))) for n in lengths]
         flops = sum(flops_per_vector(plan.K, L) for L in Ls)
-        launches = 1 + len([c for c in range(8, 17)])
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived"
         config = {"workload": "ragged leg2cheb 4096 vectors, degrees log-uniform [64, 65536), fp32, one CUDA-graph launch",
                   "K": plan.K, "coefficients": coeffs}
@@ -481,7 +485,6 @@ def run_extra(args, rank, world, local):
         coeffs, dtype = 2 * n * B, "f32"
         # both Jacobi steps: rank pairs packed, FFT length 2^21 (factor count from the plan)
         flops = 2 * flops_per_vector(pj.K, 1 << 21) / 2 * B
-        launches = None
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived (Jacobi multi-pass part)"
         config = {"workload": "jacobi (0.1,-0.3)->(0,0) + ultraspherical 0.25->1.25, n=2^20, batch=16, fp32 execute, fp64 plan, tol 1e-13",
                   "K_jacobi_max_step": pj.K}
@@ -503,7 +506,6 @@ def run_extra(args, rank, world, local):
             (wgt * beta * beta).sum().backward()
         coeffs, dtype = n * B, "f32"
         flops = 2 * flops_per_vector(plan.K, 8192) * B
-        launches = 2
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived"
         config = {"workload": "autograd leg2cheb n=8192 batch=1024 fp32: forward + loss + backward (adjoint kernel)", "K": plan.K}
         def check():
@@ -522,6 +524,8 @@ def run_extra(args, rank, world, local):
     for _ in range(args.warmup):
         fn()
     torch.cuda.synchronize()
+    if w == "c4":
+        ev_mid.clear()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -529,12 +533,16 @@ def run_extra(args, rank, world, local):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        launches0 = tdh.launch_count()
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
             evs[i][0].record(stream)
             fn()
             evs[i][1].record(stream)
         torch.cuda.synchronize()
+        launches = tdh.launch_count() - launches0
+    if w == "c3":  # graph replays launch the captured kernels without calling the library
+        launches = graph_launches * args.steps
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     if world > 1:
@@ -553,6 +561,25 @@ def run_extra(args, rank, world, local):
         extra["banded_roofline"] = {"bound": "hbm", "achieved": band_gbs, "peak": hbm_peak, "unit": "GB/s",
                                     "frac": band_gbs / hbm_peak, "traffic": None,
                                     "note": "8 algorithmic bytes per coefficient; of measured"}
+        # supplementary, outside the timed value: the downward step C^(1.25) -> C^(0.25)
+        # (back-substitution, tiled scan) on the same vectors
+        pdn = tdh.Plan("ultra2ultra", n, prec="fp32", tol=1e-13, params=(1.25, 0.25))
+        for _ in range(args.warmup):
+            pdn.execute(x, out=yu)
+        dn_ms = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pdn.execute(x, out=yu)
+            b.record(stream)
+            torch.cuda.synchronize()
+            dn_ms.append(a.elapsed_time(b))
+        dn_gbs = 8.0 * n * B / (statistics.mean(dn_ms) / 1e3) / 1e9
+        extra["backsub_roofline"] = {"bound": "hbm", "achieved": dn_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": dn_gbs / hbm_peak, "traffic": None, "ms": statistics.mean(dn_ms),
+                                     "note": "ultraspherical 1.25 -> 0.25 (three scan kernels), 8 algorithmic "
+                                             "bytes per coefficient; of measured; not part of value"}
     err = check() if (check and rank == 0) else None
     # end to end through the public API with pinned host buffers
     for _ in range(2):
@@ -576,7 +603,9 @@ def run_extra(args, rank, world, local):
                 "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                              "frac": achieved / peak, "traffic": None, "peak_note": pnote},
                 "e2e": {"value": e2e, "unit": "coeffs/s", "h2d_bytes_per_step": io, "d2h_bytes_per_step": io},
-                "gpu_launches": launches * args.steps if launches else None,
+                "gpu_launches": launches,
+                "gpu_launches_source": ("tdh_launch_count during the graph capture x replays" if w == "c3"
+                                        else "tdh_launch_count over the timed region"),
                 "clocks": sampler.summary(), "cpu_baseline": None}
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -20,6 +20,10 @@
  *     available from tdh_last_error() (thread-local) and no output is written unless stated.
  *   - The library is single-GPU: a plan belongs to the device that was current at creation
  *     and must be used with that device current.
+ *   - Scratch: execute calls take temporary device memory stream-ordered from one memory
+ *     pool per device owned by the library (cudaMallocFromPoolAsync), whose freed blocks stay
+ *     mapped for later calls (release threshold unlimited).  The first execute on a device
+ *     creates the pool, so make it outside stream capture.
  */
 #ifndef TDH_H
 #define TDH_H
@@ -127,7 +131,7 @@ int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, 
  * one thread-block cluster.  Vectors are grouped by FFT length on the device; each length
  * class is converted by one persistent launch that takes vectors from a work counter, and the
  * classes run concurrently on plan-owned streams forked from `stream` (capturable in a CUDA
- * graph).  Asynchronous; scratch is stream-ordered (cudaMallocAsync).
+ * graph).  Asynchronous; scratch is stream-ordered (see Scratch below).
  */
 int tdh_plan_execute_ragged(tdh_plan_t plan, const void* in, void* out, const int64_t* offsets,
                             int64_t batch, void* stream);
@@ -153,6 +157,15 @@ int tdh_plan_destroy(tdh_plan_t plan);
 
 /* tdh_last_error -- message of the last failing call on this thread ("" if none). */
 const char* tdh_last_error(void);
+
+/*
+ * tdh_launch_count -- instrumentation (the paper has no counterpart): *count (host) receives
+ * the number of kernel launches the library has enqueued for execute calls
+ * (tdh_plan_execute, _ragged, _adjoint) in this process since it was loaded, all devices
+ * and threads together.  Plan creation and the step entry points are not counted.
+ * Errors: INVALID_ARG (NULL count).
+ */
+int tdh_launch_count(int64_t* count);
 
 /*
  * tdh_symbols -- step a1 on its own: the split A = D1 (T o H) D2 of `kind` for n

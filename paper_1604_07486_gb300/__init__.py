@@ -22,7 +22,7 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "NOMEM", -4: "ALIGN
 # Every entry point include/tdh.h declares (checked by the CPU test suite).
 EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "tdh_plan_query",
            "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol", "tdh_pchol_noalloc",
-           "tdh_plan_execute_ragged")
+           "tdh_plan_execute_ragged", "tdh_launch_count")
 FLAG_RAGGED = 1
 
 
@@ -66,6 +66,7 @@ def lib():
         L.tdh_symbols.argtypes = [ctypes.c_int, i64, ctypes.POINTER(dbl), vp, vp, vp, vp, vp]
         L.tdh_pchol.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
         L.tdh_pchol_noalloc.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
+        L.tdh_launch_count.argtypes = [ctypes.POINTER(i64)]
         for name in EXPORTS:
             if name != "tdh_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -200,3 +201,10 @@ def pchol(h, n, j0, tol, kmax=128, stream=None):
                            ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(piv.data_ptr()),
                            ctypes.byref(K), _stream(stream)))
     return u[: K.value].clone(), piv[: K.value].clone()
+
+
+def launch_count():
+    """Kernel launches the library has enqueued for execute calls so far (tdh_launch_count)."""
+    c = ctypes.c_int64()
+    _check(lib().tdh_launch_count(ctypes.byref(c)))
+    return int(c.value)

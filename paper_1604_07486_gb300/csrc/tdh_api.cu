@@ -1,9 +1,11 @@
 // C ABI: plan construction (Fig. 1 steps 1-2), execution (steps 3-5), queries, errors.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "tdh_internal.cuh"
@@ -12,7 +14,10 @@ namespace tdh {
 
 namespace {
 thread_local char g_err[1024];
+std::atomic<int64_t> g_launches{0};
 }
+
+void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -38,6 +43,50 @@ int dev_alloc(void** p, size_t bytes) {
 
 void dev_free(void* p) {
     if (p) cudaFree(p);
+}
+
+// Execute-time scratch comes from one library-owned memory pool per device whose release
+// threshold is unlimited: freed blocks stay mapped for the next call instead of returning to
+// the driver at every synchronisation (the default pool's behaviour), which would make each
+// execute map its scratch again.
+int scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[128] = {};
+    *p = nullptr;
+    int dev = 0;
+    TDH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) {
+        set_error("device index %d out of range", dev);
+        return TDH_ERR_UNSUPPORTED;
+    }
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t created = nullptr;
+            TDH_CUDA(cudaMemPoolCreate(&created, &props));
+            uint64_t keep = UINT64_MAX;
+            TDH_CUDA(cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep));
+            pools[dev] = created;
+        }
+        pool = pools[dev];
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_error("scratch allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? TDH_ERR_NOMEM : TDH_ERR_CUDA;
+    }
+    return TDH_OK;
+}
+
+void scratch_free(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
 }
 
 int sm_count() {
@@ -284,6 +333,16 @@ using namespace tdh;
 extern "C" {
 
 const char* tdh_last_error(void) { return g_err; }
+
+int tdh_launch_count(int64_t* count) {
+    clear_error();
+    if (!count) {
+        set_error("NULL count");
+        return TDH_ERR_INVALID_ARG;
+    }
+    *count = g_launches.load(std::memory_order_relaxed);
+    return TDH_OK;
+}
 
 int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double tol,
                     tdh_plan_t* out) {

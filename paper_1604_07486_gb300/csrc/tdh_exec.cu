@@ -428,7 +428,7 @@ int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t
     }
     int* scratch = nullptr;
     const size_t words = 2 * (size_t)ncls + (size_t)ncls * batch;
-    TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(int) * words, s));
+    TDH_TRY(scratch_alloc(reinterpret_cast<void**>(&scratch), sizeof(int) * words, s));
     int* count = scratch;
     int* next = scratch + ncls;
     int* list = scratch + 2 * ncls;
@@ -436,6 +436,7 @@ int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * 2 * ncls, s);
     if (e == cudaSuccess) {
         k_classify<<<blocks_for(batch), kThreads, 0, s>>>(offs, batch, st.n, ncls, count, list);
+        note_launches(1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
@@ -478,11 +479,7 @@ int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t
         set_error("ragged execute: %s", cudaGetErrorString(e));
         rc = TDH_ERR_CUDA;
     }
-    cudaError_t ef = cudaFreeAsync(scratch, s);
-    if (rc == TDH_OK && ef != cudaSuccess) {
-        set_error("cudaFreeAsync: %s", cudaGetErrorString(ef));
-        rc = TDH_ERR_CUDA;
-    }
+    scratch_free(scratch, s);
     return rc;
 }
 

@@ -638,6 +638,7 @@ int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
         const int64_t nclusters = std::max<int64_t>(1, std::min<int64_t>(batch, resident));
         cfg.gridDim = dim3((unsigned)(nclusters * C), 1, 1);
         TDH_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
+        note_launches(1);
         return TDH_OK;
     } else {
         // balanced split: one wave of G clusters, at most one per (vector, rank term) unit
@@ -653,17 +654,19 @@ int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
                 set_error("balanced split: too many clusters");
                 return TDH_ERR_UNSUPPORTED;
             }
-            TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&P.partial),
-                                     sizeof(T) * (size_t)(2 * G) * (size_t)P.n, s));
+            TDH_TRY(scratch_alloc(reinterpret_cast<void**>(&P.partial),
+                                  sizeof(T) * (size_t)(2 * G) * (size_t)P.n, s));
         }
         cfg.gridDim = dim3((unsigned)(G * C), 1, 1);
         cudaError_t e = cudaLaunchKernelEx(&cfg, kern, P);
+        if (e == cudaSuccess) note_launches(1);
         if (e == cudaSuccess && split) {
             dim3 fg((unsigned)((P.n + 255) / 256), (unsigned)(G - 1), 1);
             k_balance_fixup<T><<<fg, 256, 0, s>>>(P.partial, P.out, P.n, U, Ku, G);
             e = cudaGetLastError();
+            if (e == cudaSuccess) note_launches(1);
         }
-        if (P.partial) cudaFreeAsync(P.partial, s);
+        if (P.partial) scratch_free(P.partial, s);
         TDH_CUDA(e);
         return TDH_OK;
     }

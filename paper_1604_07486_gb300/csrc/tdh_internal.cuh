@@ -38,8 +38,14 @@ int dev_alloc_t(T** p, size_t count) {
     return dev_alloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 void dev_free(void* p);
+// Stream-ordered execute scratch from the library's per-device pool (kept mapped).
+int scratch_alloc(void** p, size_t bytes, cudaStream_t s);
+void scratch_free(void* p, cudaStream_t s);
 
 int sm_count();
+
+// Count kernel launches made by execute calls (reported by tdh_launch_count).
+void note_launches(int64_t k);
 
 // ----------------------------------------------------------------------------- a1
 // Fill t[n], h[2n-1], d1[n], d2[n] (device, float64) for `kind`; p = kind parameters.

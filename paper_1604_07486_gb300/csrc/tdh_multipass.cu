@@ -10,7 +10,7 @@
 //              DFT, conjugate twiddle (radix 16 x C/16 in registers for 16 <= C <= 256)
 //   mp_inv   : inverse local DIT passes, W[b][k1][k2] += u_r o y
 // then beta = D1 W (D2 for the adjoint).  Scratch (v, Y, W) is stream-ordered
-// (cudaMallocAsync) and vectors are processed in chunks that bound it.
+// (the library's stream-ordered pool) and vectors are processed in chunks that bound it.
 #include <algorithm>
 #include <mutex>
 
@@ -386,6 +386,7 @@ int cross16_launch(const MPParams<T>& Q, int64_t nb, cudaStream_t s) {
         return TDH_ERR_CUDA;
     }
     mp_cross16<T, LC, C><<<dim3(LC / PP, (unsigned)nb), 256, smem, s>>>(Q);
+    note_launches(1);
     return TDH_OK;
 }
 
@@ -400,6 +401,7 @@ int cross_launch(const MPParams<T>& Q, int64_t nb, size_t smem_cross, cudaStream
     case 256: return cross16_launch<T, LC, 256>(Q, nb, s);
     default:
         mp_cross<T, LC><<<dim3(LC / 16, (unsigned)nb), 256, smem_cross, s>>>(Q);
+        note_launches(1);
         return TDH_OK;
     }
 }
@@ -465,7 +467,7 @@ int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjo
     chunk = std::min(chunk, batch);
     char* scratch = nullptr;
     const size_t bytes = per_vec * (size_t)chunk + 256;
-    TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, s));
+    TDH_TRY(scratch_alloc(reinterpret_cast<void**>(&scratch), bytes, s));
     P.vdec = reinterpret_cast<V*>(scratch);
     P.W = P.vdec + (size_t)chunk * P.L / 2;
     P.Y = P.W + (size_t)chunk * P.L / 2;
@@ -499,26 +501,25 @@ int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjo
         const unsigned ew = (unsigned)std::min<int64_t>((nb * P.L / 2 + kEw - 1) / kEw, 4096);
         mp_load<T, LC><<<ew, kEw, 0, s>>>(Q, 0, nb);
         if (P.row0) mp_row0<T><<<(unsigned)nb, kEw, 0, s>>>(Q, 0);
+        note_launches(P.row0 ? 2 : 1);
         for (int64_t r = 0; rc == TDH_OK && r < P.K; ++r) {
             mp_fwd<T, LOGLC, R, NT><<<(unsigned)(nb * P.C), NT, smem_pass, s>>>(Q, r);
             rc = cross_launch<T, LC>(Q, nb, smem_cross, s);
             mp_inv<T, LOGLC, R, NT><<<(unsigned)(nb * P.C), NT, smem_pass, s>>>(Q, r);
+            note_launches(2);
         }
         if (rc != TDH_OK) break;
         Q.in = P.in;
         const unsigned eo = (unsigned)std::min<int64_t>((nb * P.n + kEw - 1) / kEw, 4096);
         mp_store<T, LC><<<eo, kEw, 0, s>>>(Q, b0, nb);
+        note_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
             set_error("multi-pass launch: %s", cudaGetErrorString(e));
             rc = TDH_ERR_CUDA;
         }
     }
-    cudaError_t e = cudaFreeAsync(scratch, s);
-    if (rc == TDH_OK && e != cudaSuccess) {
-        set_error("cudaFreeAsync: %s", cudaGetErrorString(e));
-        rc = TDH_ERR_CUDA;
-    }
+    scratch_free(scratch, s);
     return rc;
 }
 

@@ -24,6 +24,7 @@
 // forms rounded once to the execute precision, so the kernels do no division.  All of this
 // is ~3 flops per 8 bytes moved: bound by HBM.
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "tdh_internal.cuh"
@@ -35,11 +36,11 @@ constexpr int kThreads = 256;
 constexpr int kTile = 2048;     // forward factors: coefficients per block
 constexpr int kMaxM = 16;       // factors per step
 constexpr int kInvRows = 5;     // table rows of an inverse factor
-// back-substitution: E coefficients per thread (a tile of 2048 floats or 1024 doubles, so the
-// three staged arrays stay near 25 KB), one padding slot per 128 bytes
+// back-substitution: E coefficients per thread (a tile of 4096 floats or 2048 doubles; the
+// three staged arrays take 50 KB of dynamic shared memory), one padding slot per 128 bytes
 template <typename T>
 struct Scan {
-    static constexpr int E = 32 / (int)sizeof(T);
+    static constexpr int E = 64 / (int)sizeof(T);
     static constexpr int tile = kThreads * E;
     static constexpr int per_pad = 128 / (int)sizeof(T);
     static constexpr int smem = tile + tile / per_pad;
@@ -297,10 +298,25 @@ __device__ __forceinline__ Aff<T, OFF> aff_id() {
     return r;
 }
 
+// expm1(L) for |L| <= 1/2 by its Taylor series (float: degree 9, remainder below 2^-26 of
+// the result); double uses the library function.
+__device__ __forceinline__ float expm1_small(float L) {
+    float t = 1.0f + L * (1.0f / 9.0f);
+    t = 1.0f + L * (1.0f / 8.0f) * t;
+    t = 1.0f + L * (1.0f / 7.0f) * t;
+    t = 1.0f + L * (1.0f / 6.0f) * t;
+    t = 1.0f + L * (1.0f / 5.0f) * t;
+    t = 1.0f + L * (1.0f / 4.0f) * t;
+    t = 1.0f + L * (1.0f / 3.0f) * t;
+    t = 1.0f + L * 0.5f * t;
+    return L * t;
+}
+__device__ __forceinline__ double expm1_small(double L) { return expm1(L); }
+
 // exp(L) x: near m = 1 as x + expm1(L) x (relative accuracy of m - 1 kept)
 template <typename T>
 __device__ __forceinline__ T mul_m(T L, T x) {
-    return L > T(-0.5) ? fma(expm1(L), x, x) : exp(L) * x;
+    return L > T(-0.5) ? fma(expm1_small(L), x, x) : exp(L) * x;
 }
 
 // x first, then y
@@ -331,9 +347,11 @@ template <typename T>
 __device__ __forceinline__ int spad(int i) { return i + i / Scan<T>::per_pad; }
 
 // Exclusive block scan of the threads' maps (thread order); *total = all threads' map.
+// warp_tot: [kThreads / 32 + 1] shared scratch.
 template <typename T, int OFF>
 __device__ Aff<T, OFF> block_exclusive(const Aff<T, OFF>& mine, Aff<T, OFF>* warp_tot,
                                        Aff<T, OFF>* total) {
+    constexpr int NW = kThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Aff<T, OFF> inc = mine;
 #pragma unroll
@@ -345,14 +363,23 @@ __device__ Aff<T, OFF> block_exclusive(const Aff<T, OFF>& mine, Aff<T, OFF>* war
     if (lane == 0) exl = aff_id<T, OFF>();
     if (lane == 31) warp_tot[warp] = inc;
     __syncthreads();
-    Aff<T, OFF> pre = aff_id<T, OFF>();
-    for (int w = 0; w < warp; ++w) pre = aff_then(pre, warp_tot[w]);
-    if (total) {
-        Aff<T, OFF> t = aff_id<T, OFF>();
-        for (int w = 0; w < kThreads / 32; ++w) t = aff_then(t, warp_tot[w]);
-        *total = t;
+    if (warp == 0) {
+        // exclusive scan of the warp totals by the first warp; the total goes to slot NW
+        Aff<T, OFF> v = lane < NW ? warp_tot[lane] : aff_id<T, OFF>();
+#pragma unroll
+        for (int k = 1; k < NW; k <<= 1) {
+            const Aff<T, OFF> o = aff_shfl_up(v, k);
+            if (lane >= k) v = aff_then(o, v);
+        }
+        Aff<T, OFF> ex = aff_shfl_up(v, 1);
+        if (lane == 0) ex = aff_id<T, OFF>();
+        __syncwarp();
+        if (lane < NW) warp_tot[lane] = ex;
+        if (lane == NW - 1) warp_tot[NW] = v;
     }
-    return aff_then(pre, exl);
+    __syncthreads();
+    if (total) *total = warp_tot[NW];
+    return aff_then(warp_tot[warp], exl);
 }
 
 // Logical position l runs in recurrence order: physical index l (REV = 0, x_k depends on
@@ -363,19 +390,34 @@ template <typename T, int REV>
 __device__ void scan_load(const T* x, int64_t n, int64_t l0, const T* __restrict__ rho,
                           const T* __restrict__ delta, const T* __restrict__ logm, int flip,
                           T* sb, T* sd, T* sl) {
-    for (int i = threadIdx.x; i < Scan<T>::tile; i += kThreads) {
-        const int64_t l = l0 + i;
-        T bv = T(0), dv = T(0), lv = T(0);
-        if (l < n) {
-            const int64_t j = REV ? n - 1 - l : l;
-            bv = rho[j] * x[j];
-            if (flip && (j & 1)) bv = -bv;
-            dv = delta[j];
-            lv = logm[j];
+    constexpr int IT = Scan<T>::tile / kThreads, BATCH = 8;
+    static_assert(IT % BATCH == 0, "load batches");
+#pragma unroll
+    for (int i0 = 0; i0 < IT; i0 += BATCH) {
+        // all loads of a batch first (independent, in flight together), then the stores
+        T bv[BATCH], dv[BATCH], lv[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int i = threadIdx.x + (i0 + u) * kThreads;
+            const int64_t l = l0 + i;
+            bv[u] = T(0);
+            dv[u] = T(0);
+            lv[u] = T(0);
+            if (l < n) {
+                const int64_t j = REV ? n - 1 - l : l;
+                bv[u] = rho[j] * x[j];
+                if (flip && (j & 1)) bv[u] = -bv[u];
+                dv[u] = delta[j];
+                lv[u] = logm[j];
+            }
         }
-        sb[spad<T>(i)] = bv;
-        sd[spad<T>(i)] = dv;
-        sl[spad<T>(i)] = lv;
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const int i = threadIdx.x + (i0 + u) * kThreads;
+            sb[spad<T>(i)] = bv[u];
+            sd[spad<T>(i)] = dv[u];
+            sl[spad<T>(i)] = lv[u];
+        }
     }
 }
 
@@ -400,8 +442,11 @@ __global__ void __launch_bounds__(kThreads) k_scan_tiles(const T* __restrict__ i
                                                          const T* __restrict__ delta,
                                                          const T* __restrict__ logm, int flip,
                                                          Aff<T, OFF>* __restrict__ sum) {
-    __shared__ T sb[Scan<T>::smem], sd[Scan<T>::smem], sl[Scan<T>::smem];
-    __shared__ Aff<T, OFF> wt[kThreads / 32];
+    extern __shared__ __align__(16) unsigned char scan_smem[];
+    T* sb = reinterpret_cast<T*>(scan_smem);
+    T* sd = sb + Scan<T>::smem;
+    T* sl = sd + Scan<T>::smem;
+    __shared__ Aff<T, OFF> wt[kThreads / 32 + 1];
     const int64_t vec = blockIdx.x / ntiles, tile = blockIdx.x % ntiles;
     scan_load<T, REV>(in + vec * n, n, tile * Scan<T>::tile, rho, delta, logm, flip, sb, sd, sl);
     __syncthreads();
@@ -416,7 +461,7 @@ template <typename T, int OFF>
 __global__ void __launch_bounds__(kThreads) k_scan_carry(const Aff<T, OFF>* __restrict__ sum,
                                                          int64_t ntiles,
                                                          Aff<T, OFF>* __restrict__ carry) {
-    __shared__ Aff<T, OFF> wt[kThreads / 32];
+    __shared__ Aff<T, OFF> wt[kThreads / 32 + 1];
     const Aff<T, OFF>* s = sum + (int64_t)blockIdx.x * ntiles;
     Aff<T, OFF>* cr = carry + (int64_t)blockIdx.x * ntiles;
     const int64_t per = (ntiles + kThreads - 1) / kThreads;
@@ -439,8 +484,11 @@ __global__ void __launch_bounds__(kThreads) k_scan_solve(const T* in, T* out, in
                                                          const T* __restrict__ delta,
                                                          const T* __restrict__ logm, int flip,
                                                          const Aff<T, OFF>* __restrict__ carry) {
-    __shared__ T sb[Scan<T>::smem], sd[Scan<T>::smem], sl[Scan<T>::smem];
-    __shared__ Aff<T, OFF> wt[kThreads / 32];
+    extern __shared__ __align__(16) unsigned char scan_smem[];
+    T* sb = reinterpret_cast<T*>(scan_smem);
+    T* sd = sb + Scan<T>::smem;
+    T* sl = sd + Scan<T>::smem;
+    __shared__ Aff<T, OFF> wt[kThreads / 32 + 1];
     const int64_t vec = blockIdx.x / ntiles, tile = blockIdx.x % ntiles;
     const int64_t l0 = tile * Scan<T>::tile;
     scan_load<T, REV>(in + vec * n, n, l0, rho, delta, logm, flip, sb, sd, sl);
@@ -485,6 +533,7 @@ int forward_typed(const Step& st, const void* in, void* out, int64_t batch, int 
             reinterpret_cast<const float4*>(tab), reinterpret_cast<const float4*>(tab + st.sp_ld),
             adjoint);
         TDH_CUDA(cudaGetLastError());
+        note_launches(1);
         return TDH_OK;
     }
     const int64_t ntiles = (n + kTile - 1) / kTile;
@@ -496,15 +545,17 @@ int forward_typed(const Step& st, const void* in, void* out, int64_t batch, int 
     T* halo = nullptr;
     if (inplace) {
         const int64_t total = batch * ntiles * H;
-        TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&halo), sizeof(T) * total, s));
+        TDH_TRY(scratch_alloc(reinterpret_cast<void**>(&halo), sizeof(T) * total, s));
         k_halo_save<T><<<blocks_for(total), kThreads, 0, s>>>(static_cast<const T*>(in), halo, n,
                                                                ntiles, H, adjoint, total);
+        note_launches(1);
     }
     k_fwd_tile<T, OFF><<<(unsigned)(batch * ntiles), kThreads, 0, s>>>(
         static_cast<const T*>(in), static_cast<T*>(out), n, ntiles, tab, st.sp_ld, st.sp_M,
         adjoint, halo);
     cudaError_t e = cudaGetLastError();
-    if (halo) cudaFreeAsync(halo, s);
+    if (e == cudaSuccess) note_launches(1);
+    if (halo) scratch_free(halo, s);
     TDH_CUDA(e);
     return TDH_OK;
 }
@@ -519,8 +570,22 @@ int inverse_typed(const Step& st, const void* in, void* out, int64_t batch, int 
         return TDH_ERR_UNSUPPORTED;
     }
     using A = Aff<T, OFF>;
+    constexpr size_t smem = 3 * sizeof(T) * (size_t)Scan<T>::smem;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        const void* ks[4] = {(const void*)k_scan_tiles<T, OFF, 0>, (const void*)k_scan_tiles<T, OFF, 1>,
+                             (const void*)k_scan_solve<T, OFF, 0>, (const void*)k_scan_solve<T, OFF, 1>};
+        for (const void* k : ks)
+            if (attr == cudaSuccess)
+                attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr != cudaSuccess) {
+        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(attr));
+        return TDH_ERR_CUDA;
+    }
     A *sum = nullptr, *carry = nullptr;
-    TDH_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&sum), sizeof(A) * batch * ntiles * 2, s));
+    TDH_TRY(scratch_alloc(reinterpret_cast<void**>(&sum), sizeof(A) * batch * ntiles * 2, s));
     carry = sum + batch * ntiles;
     const unsigned grid = (unsigned)(batch * ntiles);
     cudaError_t e = cudaSuccess;
@@ -534,21 +599,22 @@ int inverse_typed(const Step& st, const void* in, void* out, int64_t batch, int 
         if (!adjoint) {
             const T* dl = tab + st.sp_ld;
             const T* lg = tab + 2 * st.sp_ld;
-            k_scan_tiles<T, OFF, 1><<<grid, kThreads, 0, s>>>(src, n, ntiles, rho, dl, lg, flip, sum);
+            k_scan_tiles<T, OFF, 1><<<grid, kThreads, smem, s>>>(src, n, ntiles, rho, dl, lg, flip, sum);
             k_scan_carry<T, OFF><<<(unsigned)batch, kThreads, 0, s>>>(sum, ntiles, carry);
-            k_scan_solve<T, OFF, 1><<<grid, kThreads, 0, s>>>(src, static_cast<T*>(out), n, ntiles,
+            k_scan_solve<T, OFF, 1><<<grid, kThreads, smem, s>>>(src, static_cast<T*>(out), n, ntiles,
                                                               rho, dl, lg, flip, carry);
         } else {
             const T* dl = tab + 3 * st.sp_ld;
             const T* lg = tab + 4 * st.sp_ld;
-            k_scan_tiles<T, OFF, 0><<<grid, kThreads, 0, s>>>(src, n, ntiles, rho, dl, lg, flip, sum);
+            k_scan_tiles<T, OFF, 0><<<grid, kThreads, smem, s>>>(src, n, ntiles, rho, dl, lg, flip, sum);
             k_scan_carry<T, OFF><<<(unsigned)batch, kThreads, 0, s>>>(sum, ntiles, carry);
-            k_scan_solve<T, OFF, 0><<<grid, kThreads, 0, s>>>(src, static_cast<T*>(out), n, ntiles,
+            k_scan_solve<T, OFF, 0><<<grid, kThreads, smem, s>>>(src, static_cast<T*>(out), n, ntiles,
                                                               rho, dl, lg, flip, carry);
         }
         e = cudaGetLastError();
+        if (e == cudaSuccess) note_launches(3);
     }
-    cudaFreeAsync(sum, s);
+    scratch_free(sum, s);
     TDH_CUDA(e);
     return TDH_OK;
 }

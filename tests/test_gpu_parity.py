@@ -427,3 +427,15 @@ def test_laguerre(tdh, params, prec):
     t = oracle.split(oracle.LAG, params, n)[0]
     scale = max(1.0, np.abs(t).max())
     assert _rel_err(y, ref, alpha) <= TOL[prec] * scale
+
+
+def test_launch_count(tdh):
+    """tdh_launch_count counts the kernels an execute call enqueues (one execute kernel, plus
+    the balanced-split fix-up when vectors are split between clusters)."""
+    torch = _torch()
+    plan = tdh.Plan("leg2cheb", 1000, prec="fp32")
+    x = torch.zeros(3, 1000, device="cuda")
+    c0 = tdh.launch_count()
+    plan.execute(x)
+    torch.cuda.synchronize()
+    assert 1 <= tdh.launch_count() - c0 <= 2
