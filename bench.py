@@ -42,6 +42,18 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+def job_throughput(total_ms, units_per_rank_step, steps, world, dist=None, device="cuda"):
+    """Whole-job throughput of replicas (no collective on the data path): every rank converts
+    its own batch; the job time is the maximum over ranks of their timed totals.
+    Returns (units per second over all ranks, max total ms)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * units_per_rank_step * steps / (total_ms / 1e3), total_ms
+
+
 def flops_per_vector(K, L):
     """Algorithmic flops of one vector: per rank term a forward and an inverse complex FFT of
     L points (5 L log2 L each), the spectrum multiply (6 L), and the scalings on the way in
@@ -278,13 +290,8 @@ def main():
     t_l2c = [e[0].elapsed_time(e[1]) for e in ev]
     t_c2l = [e[1].elapsed_time(e[2]) for e in ev]
     step_ms = [a + b for a, b in zip(t_l2c, t_c2l)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     coeffs_per_step = len(KINDS) * BATCH * N
-    value = world * coeffs_per_step * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(sum(step_ms), coeffs_per_step, args.steps, world, dist)
 
     # roofline of the execute kernel (the only kernel in the timed region)
     L = N  # parity-packed correlation of n/2 complex points, padded to n
@@ -544,12 +551,7 @@ def run_extra(args, rank, world, local):
     if w == "c3":  # graph replays launch the captured kernels without calling the library
         launches = graph_launches * args.steps
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * coeffs * args.steps / (total_ms / 1e3)
+    value, total_ms = job_throughput(sum(step_ms), coeffs, args.steps, world, dist)
     achieved = flops * args.steps / (total_ms / 1e3) / 1e12
     if w == "c4" and ev_mid:
         # split: Jacobi part vs ultraspherical (sparse factor, HBM-bound) part
