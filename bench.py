@@ -190,6 +190,57 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def cpu_model():
+    """Host CPU model (lscpu), for the record."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_fast_sample():
+    """The same algorithm (Fig. 1) on the host for comparison: float64, split and Fig. 2
+    Cholesky from the oracle (plan, not timed), then v = D2 alpha, w = sum_r u_r o
+    T(u_r o v) with every Toeplitz product by scipy.fft on all host cores, beta = D1 w (+ row 0
+    for Chebyshev-to-Legendre), 16 vectors of n = 65536, both directions."""
+    import numpy as np
+    import scipy.fft as sf
+    import oracle
+    import workloads
+    B, workers = 16, os.cpu_count() or 1
+    alpha = workloads.coefficients(N, B, decay=DECAY, seed=0)
+    L = 1
+    while L < 2 * N - 1:
+        L *= 2
+    seconds = 0.0
+    for kind, tol in ((oracle.LEG2CHEB, TOL64["leg2cheb"]), (oracle.CHEB2LEG, TOL64["cheb2leg"])):
+        t, h, d1, d2 = oracle.split(kind, None, N)
+        u, _ = oracle.hankel_factors(kind, None, N, tol)
+        spec = np.conj(sf.rfft(t, L))
+        row0 = oracle.entries(kind, None, N, 0, 1)[0] if kind == oracle.CHEB2LEG else None
+        t0 = time.perf_counter()
+        v = alpha * d2
+        w = np.zeros_like(v)
+        for ur in u:
+            y = sf.irfft(sf.rfft(v * ur, L, axis=-1, workers=workers) * spec, L, axis=-1,
+                         workers=workers)[:, :N]
+            w += ur * y
+        beta = w * d1
+        if row0 is not None:
+            beta[:, 0] = alpha @ row0
+        seconds += time.perf_counter() - t0
+    return {"value": 2 * N * B / seconds, "unit": "coeffs/s", "cores": workers,
+            "kind": "same algorithm on the host: float64, scipy.fft (pocketfft) on all cores",
+            "sample": "16 vectors of n=65536, both directions, plan not timed",
+            "seconds": seconds}
+
+
 def cpu_baseline_sample():
     """Oracle on one full vector (every row, both directions) on the host cores."""
     import oracle
@@ -201,7 +252,7 @@ def cpu_baseline_sample():
     dt = time.perf_counter() - t0
     return {"value": 2 * N / dt, "unit": "coeffs/s", "cores": oracle.threads(), "kind": "oracle",
             "sample": "one n=65536 vector, all rows, both directions (dense double-double)",
-            "seconds": dt}
+            "seconds": dt, "cpu_model": cpu_model()}
 
 
 def main():
@@ -359,9 +410,10 @@ def main():
     e2e_value = world * coeffs_per_step * e2e_steps / (e2e_ms / 1e3)
     io_bytes = len(KINDS) * BATCH * N * 4
 
-    cpu = None
+    cpu, cpu_fast = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
+        cpu_fast = cpu_fast_sample()
 
     if rank == 0:
         line = {
@@ -390,6 +442,7 @@ def main():
             "wall_s": wall,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "cpu_fast_algorithm": cpu_fast,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
