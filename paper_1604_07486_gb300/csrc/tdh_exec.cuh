@@ -420,6 +420,9 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 #pragma unroll
         for (int j = 0; j < J0; ++j) {
             const int o = tid + j * NT;
+            V ul[R / 2];  // factor values first: their L2 latency overlaps the pass
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) ul[q] = ur[o + q * S0];
             V wp[R];
             powers<R>(w0[j], wp);
             V x[R];
@@ -431,7 +434,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             dit_halfout<R>(x);
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) {
-                const V uu = ur[o + q * S0];
+                const V uu = ul[q];
                 if (P.full) {
                     acc[j][q].x = fma(uu.y, x[q].y, fma(uu.x, x[q].x, acc[j][q].x));
                 } else {

@@ -194,6 +194,12 @@ __global__ void __launch_bounds__(NT, 1) mp_inv(const MPParams<T> P, int64_t r) 
 #pragma unroll
     for (int j = 0; j < J0; ++j) {
         const int o = tid + j * NT;
+        V ul[R / 2], wl[R / 2];  // global loads first: their latency overlaps the pass
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) {
+            ul[q] = ur[o + q * S0];
+            wl[q] = w[o + q * S0];
+        }
         V wp[R];
         powers<R>(P.tw0[o], wp);
         V x[R];
@@ -205,8 +211,8 @@ __global__ void __launch_bounds__(NT, 1) mp_inv(const MPParams<T> P, int64_t r) 
         dit_halfout<R>(x);
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) {
-            const V uu = ur[o + q * S0];
-            V acc = w[o + q * S0];
+            const V uu = ul[q];
+            V acc = wl[q];
             if (P.full) {
                 acc.x = fma(uu.y, x[q].y, fma(uu.x, x[q].x, acc.x));
             } else {
