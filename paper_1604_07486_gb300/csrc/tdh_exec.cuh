@@ -305,12 +305,17 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
     for (int64_t r = r_begin; r < r_end; ++r) {
         const V* ur = P.u + ((int64_t)r * C + k1) * P.u_stride;
         // ---- forward pass 0: inputs u_r o v (upper half zero), radix R, stride S0
+        V ul0[J0][R / 2];  // the factor values of every group first: one L2 latency
+#pragma unroll
+        for (int j = 0; j < J0; ++j)
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) ul0[j][q] = ur[tid + j * NT + q * S0];
 #pragma unroll
         for (int j = 0; j < J0; ++j) {
             const int o = tid + j * NT;
             V x[R];
 #pragma unroll
-            for (int q = 0; q < R / 2; ++q) x[q] = cwmul(vbuf[o + q * S0], ur[o + q * S0]);
+            for (int q = 0; q < R / 2; ++q) x[q] = cwmul(vbuf[o + q * S0], ul0[j][q]);
             dif_halfzero<R>(x);
             V wp[R];
             powers<R>(w0[j], wp);

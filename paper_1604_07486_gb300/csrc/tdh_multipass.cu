@@ -123,12 +123,17 @@ __global__ void __launch_bounds__(NT, 1) mp_fwd(const MPParams<T> P, int64_t r) 
     const V* vs = P.vdec + (bl * P.C + k1) * (LC / 2);
     const V* ur = P.u + (r * P.C + k1) * (LC / 2);
     __syncthreads();
+    V zl[J0][R / 2];  // every global load of the pass first: one latency for all groups
+#pragma unroll
+    for (int j = 0; j < J0; ++j)
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) zl[j][q] = cwmul(vs[tid + j * NT + q * S0], ur[tid + j * NT + q * S0]);
 #pragma unroll
     for (int j = 0; j < J0; ++j) {
         const int o = tid + j * NT;
         V x[R];
 #pragma unroll
-        for (int q = 0; q < R / 2; ++q) x[q] = cwmul(vs[o + q * S0], ur[o + q * S0]);
+        for (int q = 0; q < R / 2; ++q) x[q] = zl[j][q];
         dif_halfzero<R>(x);
         V wp[R];
         powers<R>(P.tw0[o], wp);
