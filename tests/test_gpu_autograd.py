@@ -78,3 +78,21 @@ def test_gradcheck_small(tdh):
     x = torch.tensor(workloads.coefficients(40, 2, seed=2), dtype=torch.float64, device="cuda",
                      requires_grad=True)
     assert torch.autograd.gradcheck(lambda a: convert(a, plan), (x,), eps=1e-6, atol=1e-8)
+
+
+@pytest.mark.parametrize("kind,params", [("jac2jac", (0.5, 0.25, 2.5, 0.25)),
+                                         ("jac2jac", (1.75, 0.5, -0.5, 0.25)),
+                                         ("ultra2ultra", (2.25, 0.75)),
+                                         ("jac2cheb", (0.25, -0.3)),
+                                         ("lag2lag", (0.5, -0.25))],
+                         ids=["jacobi_whole_steps", "jacobi_mixed_chain", "ultra_downward",
+                              "jac2cheb", "laguerre"])
+def test_gradcheck_chains(tdh, kind, params):
+    """gradcheck through chains with sparse factors, back-substitution, reflections and the
+    Chebyshev normalisation (float64, small n: the adjoint of every step kind)."""
+    import torch
+    from paper_1604_07486_gb300.autograd import convert
+    plan = tdh.Plan(kind, 37, prec="fp64", tol=1e-16, params=params)
+    x = torch.tensor(workloads.coefficients(37, 2, seed=3), dtype=torch.float64, device="cuda",
+                     requires_grad=True)
+    assert torch.autograd.gradcheck(lambda a: convert(a, plan), (x,), eps=1e-6, atol=1e-7)

@@ -439,3 +439,25 @@ def test_launch_count(tdh):
     plan.execute(x)
     torch.cuda.synchronize()
     assert 1 <= tdh.launch_count() - c0 <= 2
+
+
+@pytest.mark.parametrize("batch", [1, 5, 35, 36, 37, 71, 144])
+def test_balanced_split_batches(tdh, batch):
+    """Batches below, at and above the number of resident clusters (36 four-CTA clusters on
+    GB300): vectors split between clusters are summed by the fix-up in cluster order, and
+    vectors owned whole by one cluster are written directly; every vector is checked."""
+    torch = _torch()
+    n = 65536
+    alpha = workloads.coefficients(n, batch, decay=0.5, seed=21)
+    plan = tdh.Plan("cheb2leg", n, prec="fp32", tol=1e-10)
+    y = plan.execute(torch.tensor(alpha, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    y = y.double().cpu().numpy()
+    rows = np.unique(np.r_[np.arange(8), n - 1 - np.arange(8),
+                           np.random.default_rng(22).integers(0, n, 16)])
+    ref = oracle.matvec(oracle.CHEB2LEG, None, alpha, rows=rows)
+    err = (np.abs(y[:, rows] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
+    assert err <= TOL["fp32"]
+    # deterministic: the same call gives the same bits
+    y2 = plan.execute(torch.tensor(alpha, dtype=torch.float32, device="cuda")).double().cpu().numpy()
+    assert np.array_equal(y, y2)
