@@ -146,6 +146,20 @@ int tdh_plan_execute_adjoint(tdh_plan_t plan, const void* in, void* out, int64_t
                              void* stream);
 
 /*
+ * tdh_plan_execute_host -- beta = A alpha (adjoint = 0) or A^T g (adjoint != 0) for `batch`
+ * vectors in HOST memory: in and out are host pointers (batch * n_max values of the plan's
+ * precision; page-locked memory lets the copies run asynchronously and overlap the work).
+ * The batch moves through the device in chunks of at least 8 MB or a quarter of the batch:
+ * the copy of one chunk in, the conversion of the previous one and the copy of the one
+ * before out overlap on the plan's two copy streams and `stream`.  Device staging comes from
+ * the library's scratch pool.  Asynchronous on `stream`: out is complete, and in may be
+ * reused, once `stream` has been synchronised.  Host-buffer calls on one plan are serialised
+ * by the library (it holds per-plan events); out must not overlap in (TDH_ERR_ALIAS).
+ */
+int tdh_plan_execute_host(tdh_plan_t plan, const void* in, void* out, int64_t batch, int adjoint,
+                          void* stream);
+
+/*
  * tdh_plan_query -- report the plan's rank and size.  K (host, may be NULL) receives the
  * largest rank over the plan's conversion steps; n_max (host, may be NULL) its length.
  */

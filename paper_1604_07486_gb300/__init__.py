@@ -22,7 +22,7 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "NOMEM", -4: "ALIGN
 # Every entry point include/tdh.h declares (checked by the CPU test suite).
 EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "tdh_plan_query",
            "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol", "tdh_pchol_noalloc",
-           "tdh_plan_execute_ragged", "tdh_launch_count")
+           "tdh_plan_execute_ragged", "tdh_launch_count", "tdh_plan_execute_host")
 FLAG_RAGGED = 1
 
 
@@ -67,6 +67,7 @@ def lib():
         L.tdh_pchol.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
         L.tdh_pchol_noalloc.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
         L.tdh_launch_count.argtypes = [ctypes.POINTER(i64)]
+        L.tdh_plan_execute_host.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
         for name in EXPORTS:
             if name != "tdh_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -134,20 +135,23 @@ class Plan:
         except Exception:
             pass
 
-    def _run(self, fn, x, out, stream):
+    def _run(self, fn, x, out, stream, adjoint=0):
         torch = _torch()
-        host = x.device.type == "cpu"
-        xd = x.to("cuda", non_blocking=True) if host else x
-        if xd.dtype != self.dtype or xd.shape[-1] != self.n or not xd.is_contiguous():
+        if x.dtype != self.dtype or x.shape[-1] != self.n or not x.is_contiguous():
             raise ValueError(f"expected a contiguous {self.dtype} tensor [..., {self.n}]")
-        batch = xd.numel() // self.n
-        od = out if (out is not None and not host) else torch.empty_like(xd)
-        _check(fn(self._h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(od.data_ptr()),
-                  batch, _stream(stream)))
-        if host:
-            res = out if out is not None else torch.empty(xd.shape, dtype=xd.dtype, pin_memory=True)
-            res.copy_(od, non_blocking=True)
+        batch = x.numel() // self.n
+        if x.device.type == "cpu":
+            # host memory: the library pipelines the copies with the conversion
+            res = out if out is not None else torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+            if res.shape != x.shape or res.dtype != x.dtype or not res.is_contiguous():
+                raise ValueError("out must be a contiguous host tensor like x")
+            _check(lib().tdh_plan_execute_host(
+                self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(res.data_ptr()), batch,
+                adjoint, _stream(stream)))
             return res
+        od = out if out is not None else torch.empty_like(x)
+        _check(fn(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(od.data_ptr()),
+                  batch, _stream(stream)))
         return od
 
     def execute(self, x, out=None, stream=None):
@@ -173,7 +177,7 @@ class Plan:
 
     def adjoint(self, g, out=None, stream=None):
         """A^T g for every vector of g (the transpose product)."""
-        return self._run(lib().tdh_plan_execute_adjoint, g, out, stream)
+        return self._run(lib().tdh_plan_execute_adjoint, g, out, stream, adjoint=1)
 
 
 def symbols(kind, n, params=(), stream=None):

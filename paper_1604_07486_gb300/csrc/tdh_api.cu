@@ -159,6 +159,15 @@ int build_step(Step& st, double tol, int64_t kmax, int prec, cudaStream_t s) {
     return exec_prepare(st, prec, s);
 }
 
+void destroy_plan_streams(tdh_plan_s* plan) {
+    for (auto ss : plan->side) cudaStreamDestroy(ss);
+    for (auto ev : plan->ev) cudaEventDestroy(ev);
+    for (auto ss : plan->hs)
+        if (ss) cudaStreamDestroy(ss);
+    for (auto ev : plan->hev)
+        if (ev) cudaEventDestroy(ev);
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 bool overlaps(const void* a, const void* b, size_t bytes) {
@@ -207,6 +216,88 @@ int run(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream,
             TDH_TRY(sparse_launch(st, plan->params.prec, src, out, batch, adjoint, s));
         else
             TDH_TRY(exec_launch(st, plan->params.prec, src, out, batch, adjoint, s));
+    }
+    return TDH_OK;
+}
+
+// Host buffers: the batch goes through the device in chunks, two device slots each way, so
+// the copy of chunk i+1 in, the conversion of chunk i and the copy of chunk i-1 out overlap
+// (copy-in stream, the caller's stream, copy-out stream).  Chunks hold at least 8 MB or a
+// quarter of the batch, whichever is larger.
+int run_host(tdh_plan_t plan, const void* h_in, void* h_out, int64_t batch, void* stream,
+             int adjoint) {
+    clear_error();
+    if (!plan) {
+        set_error("NULL plan");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch < 0) {
+        set_error("batch must be >= 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return TDH_OK;
+    if (!h_in || !h_out) {
+        set_error("NULL in/out");
+        return TDH_ERR_INVALID_ARG;
+    }
+    const size_t esz = plan->params.prec == TDH_FP32 ? 4 : 8;
+    const size_t vec_bytes = esz * (size_t)plan->n_max;
+    if (overlaps(h_in, h_out, vec_bytes * (size_t)batch)) {
+        set_error("out overlaps in");
+        return TDH_ERR_ALIAS;
+    }
+    int64_t chunk = std::max<int64_t>((int64_t)((8u << 20) / vec_bytes), (batch + 3) / 4);
+    chunk = std::max<int64_t>(1, std::min(chunk, batch));
+    const int64_t nchunks = (batch + chunk - 1) / chunk;
+    const int nslots = nchunks > 1 ? 2 : 1;
+    const size_t slot_bytes = (vec_bytes * (size_t)chunk + 255) / 256 * 256;  // aligned slots
+    std::lock_guard<std::mutex> lock(plan->host_mu);
+    cudaStream_t s = as_stream(stream);
+    cudaStream_t cin = plan->hs[0], cout = plan->hs[1];
+    cudaEvent_t* hev = plan->hev;
+    char* dev = nullptr;  // [slot][in, out]
+    TDH_TRY(scratch_alloc(reinterpret_cast<void**>(&dev), 2 * slot_bytes * nslots, s));
+    auto din = [&](int64_t i) { return dev + 2 * slot_bytes * (i % nslots); };
+    auto dout = [&](int64_t i) { return din(i) + slot_bytes; };
+    const char* hi = static_cast<const char*>(h_in);
+    char* ho = static_cast<char*>(h_out);
+    int rc = TDH_OK;
+    cudaError_t e = cudaEventRecord(hev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, hev[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, hev[0], 0);
+    for (int64_t i = 0; e == cudaSuccess && rc == TDH_OK && i < nchunks; ++i) {
+        const int sl = (int)(i % nslots);
+        const int64_t nb = std::min(chunk, batch - i * chunk);
+        const size_t bytes = vec_bytes * (size_t)nb;
+        // copy in once the conversion of the chunk that last used this slot has read it
+        if (i >= nslots) e = cudaStreamWaitEvent(cin, hev[3 + sl], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(din(i), hi + vec_bytes * (size_t)(i * chunk), bytes,
+                                cudaMemcpyHostToDevice, cin);
+        if (e == cudaSuccess) e = cudaEventRecord(hev[1 + sl], cin);
+        // convert once the chunk is in and the slot's previous result has been copied out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hev[1 + sl], 0);
+        if (e == cudaSuccess && i >= nslots) e = cudaStreamWaitEvent(s, hev[5 + sl], 0);
+        if (e != cudaSuccess) break;
+        rc = run(plan, din(i), dout(i), nb, s, adjoint);
+        if (rc != TDH_OK) break;
+        e = cudaEventRecord(hev[3 + sl], s);
+        // copy out once converted
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, hev[3 + sl], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ho + vec_bytes * (size_t)(i * chunk), dout(i), bytes,
+                                cudaMemcpyDeviceToHost, cout);
+        if (e == cudaSuccess) e = cudaEventRecord(hev[5 + sl], cout);
+    }
+    // join: the caller's stream waits for the last copy out; the slots are freed after it
+    cudaError_t ej = cudaEventRecord(hev[0], cout);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, hev[0], 0);
+    scratch_free(dev, s);
+    if (rc != TDH_OK) return rc;
+    if (e == cudaSuccess) e = ej;
+    if (e != cudaSuccess) {
+        set_error("host-buffer execute: %s", cudaGetErrorString(e));
+        return TDH_ERR_CUDA;
     }
     return TDH_OK;
 }
@@ -493,12 +584,21 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         }
         if (rc == TDH_ERR_CUDA && !tdh_last_error()[0]) set_error("stream/event creation failed");
     }
+    for (int i = 0; rc == TDH_OK && i < 2; ++i)
+        if (cudaStreamCreateWithFlags(&plan->hs[i], cudaStreamNonBlocking) != cudaSuccess) {
+            set_error("stream creation failed");
+            rc = TDH_ERR_CUDA;
+        }
+    for (int i = 0; rc == TDH_OK && i < 7; ++i)
+        if (cudaEventCreateWithFlags(&plan->hev[i], cudaEventDisableTiming) != cudaSuccess) {
+            set_error("event creation failed");
+            rc = TDH_ERR_CUDA;
+        }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (rc != TDH_OK) {
         for (auto& x : plan->steps) release_step(x);
-        for (auto ss : plan->side) cudaStreamDestroy(ss);
-        for (auto ev : plan->ev) cudaEventDestroy(ev);
+        destroy_plan_streams(plan);
         delete plan;
         return rc;
     }
@@ -544,6 +644,11 @@ int tdh_plan_execute_adjoint(tdh_plan_t plan, const void* in, void* out, int64_t
     return run(plan, in, out, batch, stream, 1);
 }
 
+int tdh_plan_execute_host(tdh_plan_t plan, const void* in, void* out, int64_t batch, int adjoint,
+                          void* stream) {
+    return run_host(plan, in, out, batch, stream, adjoint ? 1 : 0);
+}
+
 int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max) {
     clear_error();
     if (!plan) {
@@ -561,8 +666,7 @@ int tdh_plan_destroy(tdh_plan_t plan) {
     clear_error();
     if (!plan) return TDH_OK;
     for (auto& st : plan->steps) release_step(st);
-    for (auto ss : plan->side) cudaStreamDestroy(ss);
-    for (auto ev : plan->ev) cudaEventDestroy(ev);
+    destroy_plan_streams(plan);
     delete plan;
     return TDH_OK;
 }

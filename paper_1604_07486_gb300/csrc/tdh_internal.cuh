@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "tdh.h"
@@ -140,6 +141,11 @@ struct tdh_plan_s {
     std::vector<tdh::Step> steps;
     std::vector<cudaStream_t> side;  // ragged batches: one stream per length class
     std::vector<cudaEvent_t> ev;     // fork/join events (ev[0] fork, ev[1+i] joins)
+    // host-buffer execution: copy-in and copy-out streams and their events
+    // (hev[0] start, hev[1+s] copied in, hev[3+s] computed, hev[5+s] copied out, slot s < 2)
+    cudaStream_t hs[2] = {nullptr, nullptr};
+    cudaEvent_t hev[7] = {};
+    std::mutex host_mu;
 };
 
 namespace tdh {

@@ -461,3 +461,30 @@ def test_balanced_split_batches(tdh, batch):
     # deterministic: the same call gives the same bits
     y2 = plan.execute(torch.tensor(alpha, dtype=torch.float32, device="cuda")).double().cpu().numpy()
     assert np.array_equal(y, y2)
+
+
+@pytest.mark.parametrize("n,batch,pinned", [(65536, 100, True), (65537, 70, False), (1000, 3, True)],
+                         ids=["chunks_pinned", "odd_n_pageable", "one_chunk"])
+def test_execute_host_buffers(tdh, n, batch, pinned):
+    """tdh_plan_execute_host: host vectors pass through the device in overlapped chunks; the
+    result matches the device-buffer call (the chunks split the batch differently, so the two
+    agree to rounding) and the oracle; the adjoint too."""
+    torch = _torch()
+    plan = tdh.Plan("leg2cheb", n, prec="fp32", tol=1e-7)
+    alpha = workloads.coefficients(n, batch, decay=0.5, seed=23)
+    x = torch.tensor(alpha, dtype=torch.float32)
+    if pinned:
+        x = x.pin_memory()
+    y = plan.execute(x)
+    g = plan.adjoint(x)
+    torch.cuda.synchronize()
+    assert y.device.type == "cpu" and g.device.type == "cpu"
+    yd = plan.execute(x.cuda()).cpu()
+    gd = plan.adjoint(x.cuda()).cpu()
+    scale = np.abs(alpha).sum(axis=1).max()
+    assert float((y - yd).abs().max()) <= 1e-6 * scale
+    assert float((g - gd).abs().max()) <= 1e-6 * scale
+    rows = np.unique(np.r_[np.arange(8), n - 1 - np.arange(8)])
+    ref = oracle.matvec(oracle.LEG2CHEB, None, alpha[[0, batch - 1]], rows=rows)
+    got = y.double().numpy()[[0, batch - 1]][:, rows]
+    assert (np.abs(got - ref).max(axis=1) / np.abs(alpha[[0, batch - 1]]).sum(axis=1)).max() <= TOL["fp32"]
