@@ -20,6 +20,12 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
     } else {
         g->logLC = cap;
         g->C = 1 << (logL - cap);
+        if (g->C > 8 && g->C <= 128) {
+            // multi-pass: slices of half the size, two CTAs per SM (up to 256 slices, the
+            // register-DFT cross stage's limit)
+            g->logLC = cap - 1;
+            g->C = 1 << (logL - cap + 1);
+        }
     }
     if (g->C > 512) return false;  // C > 8: multi-pass through global memory
     if (prec == TDH_FP32)

@@ -108,7 +108,7 @@ __global__ void mp_row0(const MPParams<T> P, int64_t b0) {
 }
 
 template <typename T, int LOGLC, int R, int NT>
-__global__ void __launch_bounds__(NT, 1) mp_fwd(const MPParams<T> P, int64_t r) {
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_fwd(const MPParams<T> P, int64_t r) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
     constexpr int LC = G.LC(), S0 = LC / R, J0 = S0 / NT, RL = G.rad(G.np() - 1);
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(NT, 1) mp_fwd(const MPParams<T> P, int64_t r) 
 }
 
 template <typename T, int LOGLC, int R, int NT>
-__global__ void __launch_bounds__(NT, 1) mp_inv(const MPParams<T> P, int64_t r) {
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T> P, int64_t r) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
     constexpr int LC = G.LC(), S0 = LC / R, J0 = S0 / NT, RL = G.rad(G.np() - 1);
@@ -542,8 +542,12 @@ int mp_launch(const Step& st, int prec, const void* in, void* out, int64_t batch
         set_error("multi-pass cross stage supports at most 512 slices");
         return TDH_ERR_UNSUPPORTED;
     }
-    if (prec == TDH_FP32) return run_typed<float, 14, 16, 512>(st, in, out, batch, adjoint, s);
-    return run_typed<double, 13, 8, 512>(st, in, out, batch, adjoint, s);
+    // slices one below the shared-memory cap run two CTAs per SM; longer FFTs keep full slices
+    if (prec == TDH_FP32)
+        return st.ex.g.logLC == 13 ? run_typed<float, 13, 16, 256>(st, in, out, batch, adjoint, s)
+                                   : run_typed<float, 14, 16, 512>(st, in, out, batch, adjoint, s);
+    return st.ex.g.logLC == 12 ? run_typed<double, 12, 8, 256>(st, in, out, batch, adjoint, s)
+                               : run_typed<double, 13, 8, 512>(st, in, out, batch, adjoint, s);
 }
 
 }  // namespace tdh
