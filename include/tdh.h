@@ -57,7 +57,7 @@ extern "C" {
 #define TDH_ERR_UNSUPPORTED (-2) /* valid request this build does not implement            */
 #define TDH_ERR_NOMEM       (-3) /* device or host allocation failed                       */
 #define TDH_ERR_ALIGN       (-4) /* pointer not aligned to 16 bytes                         */
-#define TDH_ERR_TIMEOUT     (-5) /* a bounded device wait gave up                           */
+#define TDH_ERR_TIMEOUT     (-5) /* reserved (no entry point of this build waits on the GPU) */
 #define TDH_ERR_CUDA        (-6) /* a CUDA runtime call failed (message has the detail)     */
 #define TDH_ERR_ALIAS       (-7) /* out overlaps in where the operation forbids it          */
 
@@ -67,7 +67,7 @@ typedef struct {
     double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; LAG {a1, a2};
                      JAC2CHEB / CHEB2JAC {a, b}                                              */
     int prec;     /* TDH_FP64 or TDH_FP32: the precision of plan_execute's in/out and FFTs  */
-    int flags;    /* TDH_FLAG_* (none defined yet; pass 0)                                  */
+    int flags;    /* TDH_FLAG_RAGGED or TDH_FLAG_NONE                                       */
     int64_t kmax; /* cap on the rank of each Hankel factorisation; 0 selects 128            */
 } tdh_params;
 
@@ -88,13 +88,13 @@ typedef struct {
  *     |l2 - l1| > 1 not an integer (Case 3): whole steps with those factors until the
  *     difference is below one, then Case 2 (T o H).  Differences within 1e-14 (relative) of
  *     an integer count as integers.
- *   JAC (a, b, g, d > -1): with b != d, first b -> d in the reflected frame
- *     P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x), then a -> g; each part takes Case 1 / 4 whole
- *     steps with the bidiagonal factors S_(a,b) (inverses when lowering) and one Case 2
+ *   JAC (a, b, g, d > -1): a -> g at fixed b directly, b -> d at fixed a in the reflected
+ *     frame P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x).  Each change takes Case 1 / 4 whole steps
+ *     with the bidiagonal factors S_(a,b) (their inverses when lowering) and one Case 2
  *     (T o H) step for a fractional rest, or Case 3 (row 0 direct) when that step's source
- *     parameters sum to <= -1.  The T o H step runs at the lower end of the range (first
- *     when raising, last when lowering), where the diagonal scalings amplify the Hankel
- *     factorisation's rounding least.
+ *     parameters sum to <= -1.  Order: every downward whole step first, then the T o H steps
+ *     at the lower end of each range (where the diagonal scalings amplify the Hankel
+ *     factorisation's rounding least), then every upward whole step.
  *   JAC2CHEB / CHEB2JAC: the Jacobi chain to / from (-1/2, -1/2) with the normalisation
  *     T_k = P_k^(-1/2,-1/2) / P_k^(-1/2,-1/2)(1) folded into its last / first step.
  *   LAG (a1, a2 > -1): one Toeplitz step (H = all ones).
@@ -131,7 +131,7 @@ int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, 
  * one thread-block cluster.  Vectors are grouped by FFT length on the device; each length
  * class is converted by one persistent launch that takes vectors from a work counter, and the
  * classes run concurrently on plan-owned streams forked from `stream` (capturable in a CUDA
- * graph).  Asynchronous; scratch is stream-ordered (see Scratch below).
+ * graph).  Asynchronous; scratch is stream-ordered (see Scratch above).
  */
 int tdh_plan_execute_ragged(tdh_plan_t plan, const void* in, void* out, const int64_t* offsets,
                             int64_t batch, void* stream);
@@ -175,7 +175,7 @@ const char* tdh_last_error(void);
 /*
  * tdh_launch_count -- instrumentation (the paper has no counterpart): *count (host) receives
  * the number of kernel launches the library has enqueued for execute calls
- * (tdh_plan_execute, _ragged, _adjoint) in this process since it was loaded, all devices
+ * (tdh_plan_execute, _ragged, _adjoint, _host) in this process since it was loaded, all devices
  * and threads together.  Plan creation and the step entry points are not counted.
  * Errors: INVALID_ARG (NULL count).
  */
