@@ -352,6 +352,9 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             // CTA k1 owns positions [k1 LC/C, (k1+1) LC/C).
             constexpr int PPC = LC / C;
             static_assert(PPC % (2 * NT) == 0, "two positions per thread");
+            // float64: one complex value is already a 16-byte access, so a thread takes one
+            // position at a time (half the registers of a pair)
+            constexpr bool kPairs = sizeof(T) == 4;
             cg::cluster_group cl = cg::this_cluster();
 #pragma unroll 1
             for (int g = tid; g < LC / RL; g += NT) {
@@ -363,8 +366,35 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
                 for (int jj = 0; jj < RL; ++jj) buf[sidx<V>(g * RL + bitrev(jj, RL))] = x[jj];
             }
             cl.sync();
+            if constexpr (!kPairs) {
 #pragma unroll 1
-            for (int pi = 2 * tid; pi < PPC; pi += 2 * NT) {
+                for (int pi = tid; pi < PPC; pi += NT) {
+                    const int pos = k1 * PPC + pi;
+                    const int sp = sidx<V>(pos);
+                    V a[C], sc[C], twj[C];
+#pragma unroll
+                    for (int j = 0; j < C; ++j) a[j] = rbuf[j][sp];
+                    const V tw = P.twx[pos];
+#pragma unroll
+                    for (int f = 0; f < C; ++f) sc[f] = P.spec[(int64_t)pos * C + f];
+                    twj[0] = mk<V>(1, 0);
+#pragma unroll
+                    for (int j = 1; j < C; ++j) twj[j] = cmul(twj[j - 1], tw);
+#pragma unroll
+                    for (int j = 0; j < C; ++j) a[j] = cmul(a[j], twj[j]);
+                    dif<C>(a);
+#pragma unroll
+                    for (int ff = 0; ff < C; ++ff) {
+                        const V sv = sc[bitrev(ff, C)];
+                        a[ff] = P.adjoint ? cmulc(a[ff], sv) : cmul(a[ff], sv);
+                    }
+                    dit<C>(a);
+#pragma unroll
+                    for (int j = 0; j < C; ++j) rbuf[j][sp] = cmulc(a[j], twj[j]);
+                }
+            }
+#pragma unroll 1
+            for (int pi = 2 * tid; kPairs && pi < PPC; pi += 2 * NT) {
                 const int pos = k1 * PPC + pi;  // even: the pair (pos, pos+1) is contiguous
                 const bool swp = pair_swapped<V>(pos);
                 const int sp = sidx<V>(pos) & ~1;
