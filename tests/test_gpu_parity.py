@@ -488,3 +488,24 @@ def test_execute_host_buffers(tdh, n, batch, pinned):
     ref = oracle.matvec(oracle.LEG2CHEB, None, alpha[[0, batch - 1]], rows=rows)
     got = y.double().numpy()[[0, batch - 1]][:, rows]
     assert (np.abs(got - ref).max(axis=1) / np.abs(alpha[[0, batch - 1]]).sum(axis=1)).max() <= TOL["fp32"]
+
+
+def test_largest_supported_length_and_beyond(tdh):
+    """The largest float32 Legendre -> Chebyshev length, n = 2^23 (an FFT of 2^23 points: 512
+    slices of 16384, the multi-pass path with the general cross stage), against the oracle on
+    sampled rows; one coefficient more needs 2^24 points and is refused with UNSUPPORTED."""
+    torch = _torch()
+    n = 1 << 23
+    alpha = workloads.coefficients(n, 1, decay=0.5, seed=24)
+    plan = tdh.Plan("leg2cheb", n, prec="fp32", tol=1e-7)
+    y = plan.execute(torch.tensor(alpha, dtype=torch.float32, device="cuda"))
+    torch.cuda.synchronize()
+    rows = np.unique(np.r_[np.arange(32), n - 1 - np.arange(32),
+                           np.random.default_rng(25).integers(0, n, 64)])
+    ref = oracle.matvec(oracle.LEG2CHEB, None, alpha, rows=rows)
+    got = y.double().cpu().numpy()[:, rows]
+    assert (np.abs(got - ref).max() / np.abs(alpha).sum()) <= TOL["fp32"]
+    del plan, y
+    with pytest.raises(tdh.TdhError) as e:
+        tdh.Plan("leg2cheb", n + 1, prec="fp32", tol=1e-7)
+    assert e.value.code == -2
