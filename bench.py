@@ -54,6 +54,18 @@ def job_throughput(total_ms, units_per_rank_step, steps, world, dist=None, devic
     return world * units_per_rank_step * steps / (total_ms / 1e3), total_ms
 
 
+def tune(plan, batch, args):
+    """Pick the plan's execute schedules by timing them (tdh_plan_autotune), outside any
+    timed region; returns (milliseconds spent, the schedules in use)."""
+    t0 = time.perf_counter()
+    if not args.no_autotune:
+        plan.autotune(batch)
+    ms = 1e3 * (time.perf_counter() - t0)
+    desc = [f"L=2^{s['logL']}: LC=2^{s['logLC']} C={s['C']} NT={s['NT']} MINB={s['MINB']} "
+            f"({s['index']}/{s['count']})" for s in plan.schedules()]
+    return ms, desc
+
+
 def flops_per_vector(K, L):
     """Algorithmic flops of one vector: per rank term a forward and an inverse complex FFT of
     L points (5 L log2 L each), the spectrum multiply (6 L), and the scalings on the way in
@@ -263,6 +275,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep every plan on its default execute schedule")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
                     help="c2 (default): Leg<->Cheb n=2^16 batch 256; c1: Leg->Cheb n=1024 fp64; "
                          "c3: ragged 4096 vectors; c4: Jacobi + ultraspherical n=2^20 batch 16; "
@@ -306,6 +320,7 @@ def main():
     plans32 = {k: tdh.Plan(k, N, prec="fp32", tol=TOL32[k]) for k in KINDS}
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0) / len(KINDS)
+    tuned = {k: tune(plans32[k], BATCH, args) for k in KINDS}
 
     alpha = workloads.coefficients(N, BATCH, decay=DECAY, seed=rank)
     xs = {k: torch.tensor(alpha, dtype=torch.float32, device="cuda") for k in KINDS}
@@ -367,6 +382,7 @@ def main():
     fp64 = None
     if not args.no_fp64:
         plans64 = {k: tdh.Plan(k, N, prec="fp64", tol=TOL64[k]) for k in KINDS}
+        tuned64 = {k: tune(plans64[k], BATCH, args)[1] for k in KINDS}
         x64 = {k: torch.tensor(alpha, dtype=torch.float64, device="cuda") for k in KINDS}
         y64 = {k: torch.empty_like(x64[k]) for k in KINDS}
         step(plans64, x64, y64)
@@ -387,7 +403,7 @@ def main():
                 err64[k] = oracle_error(alpha, y64[k].cpu().numpy(), k, [0, BATCH - 1], rows)
         fp64 = {"value": world * coeffs_per_step * reps / (ms64 / 1e3), "unit": "coeffs/s",
                 "ms_per_step": ms64 / reps, "K": {k: plans64[k].K for k in KINDS},
-                "tol": TOL64, "error_vs_oracle": err64}
+                "tol": TOL64, "error_vs_oracle": err64, "schedule": tuned64}
         del plans64, x64, y64
 
     # end to end through the public API: pinned host in, host out, every step
@@ -424,6 +440,8 @@ def main():
             "config": {"workload": WORKLOAD, "n": N, "batch_per_gpu": BATCH, "kinds": list(KINDS),
                        "decay": DECAY, "K": {k: plans32[k].K for k in KINDS}, "tol": TOL32,
                        "plan_ms": plan_ms, "l2": "flushed between steps (256 MB write)",
+                       "schedule": {k: tuned[k][1] for k in KINDS},
+                       "autotune_ms": {k: tuned[k][0] for k in KINDS},
                        "parallelism": f"replicas x{world}, no collective"},
             "error_vs_oracle": err,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -474,6 +492,7 @@ def run_extra(args, rank, world, local):
     if w == "c1":
         n, B = 1024, 1
         plan = tdh.Plan("leg2cheb", n, prec="fp64", tol=1e-15)
+        tuned = {"leg2cheb": tune(plan, B, args)}
         alpha = workloads.coefficients(n, B, decay=1.0, seed=rank)
         x = torch.tensor(alpha, dtype=torch.float64, device="cuda")
         y = torch.empty_like(x)
@@ -491,6 +510,7 @@ def run_extra(args, rank, world, local):
         lengths = deg + 1
         xv, offs = workloads.ragged_coefficients(lengths, decay=1.0, seed=rank)
         plan = tdh.Plan("leg2cheb", int(lengths.max()), prec="fp32", tol=1e-7, ragged=True)
+        tuned = {"leg2cheb": tune(plan, len(lengths), args)}
         xt = torch.tensor(xv, dtype=torch.float32, device="cuda")
         ot = torch.tensor(offs, dtype=torch.int64, device="cuda")
         yt = torch.empty_like(xt)
@@ -532,6 +552,7 @@ def run_extra(args, rank, world, local):
         n, B = 1 << 20, 16
         pj = tdh.Plan("jac2jac", n, prec="fp32", tol=1e-13, params=(0.1, -0.3, 0.0, 0.0))
         pu = tdh.Plan("ultra2ultra", n, prec="fp32", tol=1e-13, params=(0.25, 1.25))
+        tuned = {"jacobi": tune(pj, B, args)}
         alpha = workloads.coefficients(n, B, decay=1.5, seed=rank)
         x = torch.tensor(alpha, dtype=torch.float32, device="cuda")
         yj, yu = torch.empty_like(x), torch.empty_like(x)
@@ -557,6 +578,7 @@ def run_extra(args, rank, world, local):
     elif w == "c5":
         n, B = 8192, 1024
         plan = tdh.Plan("leg2cheb", n, prec="fp32", tol=1e-7)
+        tuned = {"leg2cheb": tune(plan, B, args)}
         alpha = workloads.coefficients(n, B, decay=1.0, seed=rank)
         x = torch.tensor(alpha, dtype=torch.float32, device="cuda", requires_grad=True)
         wgt = (torch.arange(n, device="cuda", dtype=torch.float32) + 1.0) ** 2
@@ -579,7 +601,8 @@ def run_extra(args, rank, world, local):
         host_fn = lambda: plan.execute(host_in)
         io = n * B * 4
     torch.cuda.synchronize()
-    plan_ms = 1e3 * (time.perf_counter() - t0)
+    tune_ms = sum(t[0] for t in tuned.values())
+    plan_ms = 1e3 * (time.perf_counter() - t0) - tune_ms  # plan construction and data setup
 
     for _ in range(args.warmup):
         fn()
@@ -653,7 +676,9 @@ def run_extra(args, rank, world, local):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
                 "data": "synthetic", "config": dict(config, plan_ms=plan_ms,
-                                                    l2="flushed between steps (256 MB write)"),
+                                                    l2="flushed between steps (256 MB write)",
+                                                    schedule={k: t[1] for k, t in tuned.items()},
+                                                    autotune_ms=tune_ms),
                 "error_vs_oracle": err,
                 "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                              "frac": achieved / peak, "traffic": None, "peak_note": pnote},

@@ -165,6 +165,38 @@ int tdh_plan_execute_host(tdh_plan_t plan, const void* in, void* out, int64_t ba
  */
 int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max);
 
+/*
+ * Execute schedules (no counterpart in the paper, which fixes no GPU geometry).  Each FFT of
+ * the execute path (eq. (Cdecomposition), "O(K) FFTs of size 2N-1", Sec. 1) runs on one of
+ * several compiled schedules: local FFT length LC = 2^log2LC per CTA, C CTAs per vector (a
+ * thread-block cluster for C <= 8, a multi-pass exchange through global memory above), local
+ * radix R, NT threads per CTA, and MINB, the CTAs per SM its registers are capped for.  A
+ * plan's "configurations" are, in order: the dense configuration of each T o H step of its
+ * chain, then (TDH_FLAG_RAGGED plans) one per FFT length class 2^8, 2^9, ... .  At creation
+ * every configuration takes its default schedule (schedule 0).  Schedules differ only in
+ * the order of floating-point operations.
+ *
+ * tdh_plan_schedule_count -- *count (host) receives the number of configurations.
+ * tdh_plan_schedule_info -- info (host, 8 ints) receives, for configuration `config`:
+ *   {log2 L, log2 LC, C, R, NT, MINB, index of the schedule in use, number of schedules}.
+ *   Errors: INVALID_ARG (NULL plan/info, config out of range).
+ * tdh_plan_set_schedule -- every configuration takes its schedule min(index, count - 1) (the
+ *   execute tables are rebuilt where the schedule changes).  Synchronises `stream`.
+ * tdh_plan_autotune -- times every schedule of every configuration on synthetic input (the
+ *   dense configurations on `batch` vectors of n_max coefficients, each ragged length class on
+ *   max(1, batch / classes) vectors of the class's longest length), shortest of three
+ *   launches after one untimed, and keeps the fastest.  Uses about 2 * batch * n_max values of
+ *   device memory while it runs; synchronises `stream`.  Errors: INVALID_ARG (batch < 1),
+ *   NOMEM, CUDA.
+ * Both calls that change schedules are synchronous, must not run while executes of the plan
+ * are in flight or being captured, and free the tables the old schedule used: CUDA graphs
+ * captured from the plan before the change must not be replayed after it.
+ */
+int tdh_plan_schedule_count(tdh_plan_t plan, int* count);
+int tdh_plan_schedule_info(tdh_plan_t plan, int config, int* info);
+int tdh_plan_set_schedule(tdh_plan_t plan, int index, void* stream);
+int tdh_plan_autotune(tdh_plan_t plan, int64_t batch, void* stream);
+
 /* tdh_plan_destroy -- free the plan's device and host memory.  NULL is a no-op.  Waits for
  * nothing: the caller must not destroy a plan with launches still in flight. */
 int tdh_plan_destroy(tdh_plan_t plan);
@@ -175,8 +207,9 @@ const char* tdh_last_error(void);
 /*
  * tdh_launch_count -- instrumentation (the paper has no counterpart): *count (host) receives
  * the number of kernel launches the library has enqueued for execute calls
- * (tdh_plan_execute, _ragged, _adjoint, _host) in this process since it was loaded, all devices
- * and threads together.  Plan creation and the step entry points are not counted.
+ * (tdh_plan_execute, _ragged, _adjoint, _host, and the timed launches of tdh_plan_autotune)
+ * in this process since it was loaded, all devices and threads together.  Plan creation and
+ * the step entry points are not counted.
  * Errors: INVALID_ARG (NULL count).
  */
 int tdh_launch_count(int64_t* count);

@@ -22,7 +22,9 @@ ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "NOMEM", -4: "ALIGN
 # Every entry point include/tdh.h declares (checked by the CPU test suite).
 EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "tdh_plan_query",
            "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol", "tdh_pchol_noalloc",
-           "tdh_plan_execute_ragged", "tdh_launch_count", "tdh_plan_execute_host")
+           "tdh_plan_execute_ragged", "tdh_launch_count", "tdh_plan_execute_host",
+           "tdh_plan_schedule_count", "tdh_plan_schedule_info", "tdh_plan_set_schedule",
+           "tdh_plan_autotune")
 FLAG_RAGGED = 1
 
 
@@ -68,6 +70,10 @@ def lib():
         L.tdh_pchol_noalloc.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
         L.tdh_launch_count.argtypes = [ctypes.POINTER(i64)]
         L.tdh_plan_execute_host.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
+        L.tdh_plan_schedule_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.tdh_plan_schedule_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.tdh_plan_set_schedule.argtypes = [vp, ctypes.c_int, vp]
+        L.tdh_plan_autotune.argtypes = [vp, i64, vp]
         for name in EXPORTS:
             if name != "tdh_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -178,6 +184,31 @@ class Plan:
     def adjoint(self, g, out=None, stream=None):
         """A^T g for every vector of g (the transpose product)."""
         return self._run(lib().tdh_plan_execute_adjoint, g, out, stream, adjoint=1)
+
+    _SCHED_KEYS = ("logL", "logLC", "C", "R", "NT", "MINB", "index", "count")
+
+    def schedules(self):
+        """The execute schedule of each configuration (each T o H step, then each ragged
+        length class): dicts with log2 L, log2 LC, cluster size C, radix R, threads NT,
+        CTAs per SM MINB, and the schedule's index among `count` compiled ones."""
+        n = ctypes.c_int()
+        _check(lib().tdh_plan_schedule_count(self._h, ctypes.byref(n)))
+        out = []
+        for c in range(n.value):
+            info = (ctypes.c_int * 8)()
+            _check(lib().tdh_plan_schedule_info(self._h, c, info))
+            out.append(dict(zip(self._SCHED_KEYS, list(info))))
+        return out
+
+    def set_schedule(self, index, stream=None):
+        """Every configuration takes its schedule min(index, count - 1) (synchronous)."""
+        _check(lib().tdh_plan_set_schedule(self._h, int(index), _stream(stream)))
+
+    def autotune(self, batch, stream=None):
+        """Time every compiled schedule on `batch` synthetic vectors and keep the fastest for
+        each configuration (synchronous); returns schedules()."""
+        _check(lib().tdh_plan_autotune(self._h, int(batch), _stream(stream)))
+        return self.schedules()
 
 
 def symbols(kind, n, params=(), stream=None):

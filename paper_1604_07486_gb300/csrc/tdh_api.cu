@@ -662,6 +662,51 @@ int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max) {
     return TDH_OK;
 }
 
+int tdh_plan_schedule_count(tdh_plan_t plan, int* count) {
+    clear_error();
+    if (!plan || !count) {
+        set_error("NULL plan or count");
+        return TDH_ERR_INVALID_ARG;
+    }
+    *count = exec_schedule_count(*plan);
+    return TDH_OK;
+}
+
+int tdh_plan_schedule_info(tdh_plan_t plan, int config, int* info) {
+    clear_error();
+    if (!plan || !info) {
+        set_error("NULL plan or info");
+        return TDH_ERR_INVALID_ARG;
+    }
+    return exec_schedule_info(*plan, config, info);
+}
+
+int tdh_plan_set_schedule(tdh_plan_t plan, int index, void* stream) {
+    clear_error();
+    if (!plan) {
+        set_error("NULL plan");
+        return TDH_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(plan->host_mu);
+    cudaStream_t s = as_stream(stream);
+    const int rc = exec_set_schedule(*plan, index, s);
+    TDH_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
+int tdh_plan_autotune(tdh_plan_t plan, int64_t batch, void* stream) {
+    clear_error();
+    if (!plan) {
+        set_error("NULL plan");
+        return TDH_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(plan->host_mu);
+    cudaStream_t s = as_stream(stream);
+    const int rc = exec_autotune(*plan, batch, s);
+    TDH_CUDA(cudaStreamSynchronize(s));
+    return rc;
+}
+
 int tdh_plan_destroy(tdh_plan_t plan) {
     clear_error();
     if (!plan) return TDH_OK;

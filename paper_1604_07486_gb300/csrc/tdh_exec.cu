@@ -9,7 +9,15 @@
 namespace tdh {
 namespace {
 
-// FFT geometry for a transform of 2^logL points in precision `prec`.
+// Threads and occupancy of the multi-pass kernels for local length 2^logLC: slices one below
+// the shared-memory cap run 256 threads, two CTAs per SM; full slices 512 threads, one CTA.
+void mp_threads(int prec, int logLC, int* NT, int* MINB) {
+    const int cap = (prec == TDH_FP32) ? 14 : 13;
+    *NT = logLC == cap ? 512 : 256;
+    *MINB = logLC == cap ? 1 : 2;
+}
+
+// Default FFT geometry for a transform of 2^logL points in precision `prec`.
 bool choose_geometry(int prec, int logL, Geometry* g) {
     g->prec = prec;
     g->logL = logL;
@@ -28,14 +36,59 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
         }
     }
     if (g->C > 512) return false;  // C > 8: multi-pass through global memory
-    if (prec == TDH_FP32)
-        g->R = (g->logLC <= 9) ? 8 : 16;
-    else
-        g->R = 8;
+    g->R = radix_for(prec == TDH_FP32, g->logLC);
     g->NT = std::min(512, (1 << g->logLC) / g->R);
+    g->MINB = 1;
+    if (g->C > 8) mp_threads(prec, g->logLC, &g->NT, &g->MINB);
     return true;
 }
 
+bool same_schedule(const Geometry& a, const Geometry& b) {
+    return a.logLC == b.logLC && a.C == b.C && a.NT == b.NT && a.MINB == b.MINB;
+}
+
+// Every schedule with a compiled kernel for 2^logL points, the default first: the cluster
+// schedules of the table whose LC * C = L, and for C > 8 (not in ragged batches, which stay
+// within one cluster) the multi-pass kernels on full and on half-size slices.
+std::vector<Geometry> schedule_candidates(int prec, int logL, bool ragged) {
+    std::vector<Geometry> out;
+    Geometry d{};
+    if (!choose_geometry(prec, logL, &d)) return out;
+    out.push_back(d);
+    auto add = [&](int logLC, int C, int NT, int MINB) {
+        Geometry g = d;
+        g.logLC = logLC;
+        g.C = C;
+        g.R = radix_for(prec == TDH_FP32, logLC);
+        g.NT = NT;
+        g.MINB = MINB;
+        for (const Geometry& o : out)
+            if (same_schedule(o, g)) return;
+        out.push_back(g);
+    };
+    const bool f32 = prec == TDH_FP32;
+    const int n = f32 ? SchedTable<true>::size : SchedTable<false>::size;
+    for (int i = 0; i < n; ++i) {
+        const Sched e = f32 ? SchedTable<true>::at(i) : SchedTable<false>::at(i);
+        if (e.logLC + ilog2(e.C) == logL) add(e.logLC, e.C, e.NT, e.MINB);
+    }
+    if (!ragged) {
+        const int cap = f32 ? 14 : 13;
+        for (int lc = cap; lc >= cap - 1; --lc) {
+            if (logL - lc < 4 || logL - lc > 9) continue;  // 16 ... 512 slices
+            int NT, MINB;
+            mp_threads(prec, lc, &NT, &MINB);
+            add(lc, 1 << (logL - lc), NT, MINB);
+        }
+    }
+    if (ragged) {
+        std::vector<Geometry> in;
+        in.swap(out);
+        for (const Geometry& g : in)
+            if (g.C <= 8) out.push_back(g);
+    }
+    return out;
+}
 
 constexpr int kThreads = 256;
 inline unsigned blocks_for(int64_t count) { return (unsigned)((count + kThreads - 1) / kThreads); }
@@ -423,10 +476,41 @@ __global__ void k_classify(const int64_t* __restrict__ offs, int64_t batch, int6
 }
 
 template <typename T>
+ExecParams<T> ragged_params(const Step& st, const ExecData& ex, const void* in, void* out,
+                            const int64_t* offs, int* list, int* count, int* next, int64_t batch) {
+    using V = typename cx<T>::t;
+    ExecParams<T> P;
+    P.in = static_cast<const T*>(in);
+    P.out = static_cast<T*>(out);
+    P.n = st.n;
+    P.K = st.K;
+    P.u = static_cast<const V*>(ex.u);
+    P.spec = static_cast<const V*>(ex.spec);
+    P.twx = static_cast<const V*>(ex.twx);
+    P.tw0 = static_cast<const V*>(ex.tw0);
+    P.twp = static_cast<const V*>(ex.twp);
+    P.din = static_cast<const T*>(st.d2x);
+    P.dout = static_cast<const T*>(st.d1x);
+    P.row0 = static_cast<const T*>(st.row0);
+    P.adjoint = 0;
+    P.full = 0;
+    P.sign_in = 0;
+    P.sign_out = 0;
+    P.u_stride = ex.u_stride;
+    P.batch = batch;
+    P.partial = nullptr;
+    P.ragged = 1;
+    P.offs = offs;
+    P.list = list;
+    P.count = count;
+    P.next = next;
+    return P;
+}
+
+template <typename T>
 int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t* offs,
                         int64_t batch, cudaStream_t s, const std::vector<cudaStream_t>& side,
                         const std::vector<cudaEvent_t>& ev) {
-    using V = typename cx<T>::t;
     const int ncls = (int)st.rcls.size();
     if ((int)side.size() < ncls || (int)ev.size() < ncls + 1) {
         set_error("ragged execute: plan streams missing");
@@ -452,31 +536,8 @@ int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t
         cudaStream_t sc = side[c];
         e = cudaStreamWaitEvent(sc, ev[0], 0);
         if (e != cudaSuccess) break;
-        ExecParams<T> P;
-        P.in = static_cast<const T*>(in);
-        P.out = static_cast<T*>(out);
-        P.n = st.n;
-        P.K = st.K;
-        P.u = static_cast<const V*>(ex.u);
-        P.spec = static_cast<const V*>(ex.spec);
-        P.twx = static_cast<const V*>(ex.twx);
-        P.tw0 = static_cast<const V*>(ex.tw0);
-        P.twp = static_cast<const V*>(ex.twp);
-        P.din = static_cast<const T*>(st.d2x);
-        P.dout = static_cast<const T*>(st.d1x);
-        P.row0 = static_cast<const T*>(st.row0);
-        P.adjoint = 0;
-        P.full = 0;
-        P.sign_in = 0;
-        P.sign_out = 0;
-        P.u_stride = ex.u_stride;
-        P.batch = batch;
-        P.partial = nullptr;
-        P.ragged = 1;
-        P.offs = offs;
-        P.list = list + (int64_t)c * batch;
-        P.count = count + c;
-        P.next = next + c;
+        ExecParams<T> P = ragged_params<T>(st, ex, in, out, offs, list + (int64_t)c * batch,
+                                           count + c, next + c, batch);
         rc = dispatch<T>(ex.g, P, batch, sc);
         if (rc == TDH_OK) e = cudaEventRecord(ev[1 + c], sc);
         if (e == cudaSuccess && rc == TDH_OK) e = cudaStreamWaitEvent(s, ev[1 + c], 0);
@@ -505,11 +566,232 @@ int exec_launch(const Step& st, int prec, const void* in, void* out, int64_t bat
     return launch_typed<double>(st, in, out, batch, adjoint, s);
 }
 
-int dispatch_dense(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s) {
-    return dispatch_geom<float, false>(g, P, batch, s);
+// ----------------------------------------------------------------------------- schedules
+
+namespace {
+
+struct ConfigRef {
+    Step* st;
+    int cls;  // -1: the step's dense configuration, else its ragged length class
+};
+
+std::vector<ConfigRef> plan_configs(tdh_plan_s& plan) {
+    std::vector<ConfigRef> out;
+    for (auto& st : plan.steps) {
+        if (st.sp_M > 0) continue;
+        out.push_back({&st, -1});
+        for (int c = 0; c < (int)st.rcls.size(); ++c) out.push_back({&st, c});
+    }
+    return out;
 }
-int dispatch_dense(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s) {
-    return dispatch_geom<double, false>(g, P, batch, s);
+
+ExecData& config_data(const ConfigRef& r) { return r.cls < 0 ? r.st->ex : r.st->rcls[r.cls]; }
+
+// Rebuild configuration r's tables for schedule g (nothing to do if it already runs g).
+int rebuild_config(const ConfigRef& r, int prec, const Geometry& g, cudaStream_t s) {
+    ExecData& cur = config_data(r);
+    if (same_schedule(cur.g, g)) return TDH_OK;
+    ExecData nx;
+    nx.m = cur.m;
+    nx.g = g;
+    const bool nat = r.cls >= 0 && g.C == 1;  // ragged single-CTA classes share u_nat
+    const void* su = nat ? r.st->u_nat : nullptr;
+    const int64_t ss = nat ? (r.st->n + 1) / 2 : 0;
+    const int rc = prec == TDH_FP32 ? prepare_typed<float>(*r.st, nx, g, su, ss, s)
+                                    : prepare_typed<double>(*r.st, nx, g, su, ss, s);
+    if (rc != TDH_OK) {
+        exec_release(nx);
+        return rc;
+    }
+    exec_release(cur);
+    cur = nx;
+    return TDH_OK;
+}
+
+// Deterministic test values in [-1, 1) (an integer hash of the index, then scaled).
+template <typename T>
+__global__ void k_fill_test(T* __restrict__ x, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= count) return;
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 29;
+    x[i] = (T)((double)(z >> 11) * 0x1.0p-52 - 1.0);
+}
+
+// Uniform ragged batch for timing one length class: b vectors of length len.
+__global__ void k_ragged_uniform(int64_t* __restrict__ offs, int* __restrict__ list,
+                                 int* __restrict__ ctr, int64_t b, int64_t len) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < b) list[i] = (int)i;
+    if (i <= b) offs[i] = i * len;
+    if (i == 0) {
+        ctr[0] = (int)b;
+        ctr[1] = 0;
+    }
+}
+
+struct TuneBuffers {
+    void* in = nullptr;
+    void* out = nullptr;
+    int64_t* offs = nullptr;
+    int* list = nullptr;
+    int* ctr = nullptr;
+    cudaEvent_t ev[4] = {};
+};
+
+// Vectors and length each timing of configuration r uses.
+void tune_shape(const ConfigRef& r, int64_t batch, int64_t* b, int64_t* len) {
+    if (r.cls < 0) {
+        *b = batch;
+        *len = r.st->n;
+        return;
+    }
+    const int64_t ncls = (int64_t)r.st->rcls.size();
+    *b = std::max<int64_t>(1, batch / ncls);
+    *len = std::min<int64_t>(r.st->n, (int64_t)1 << r.st->rcls[r.cls].g.logL);
+}
+
+// Shortest of three timed launches of configuration r (after one untimed).
+template <typename T>
+int time_config(const ConfigRef& r, int64_t batch, const TuneBuffers& tb, cudaStream_t s,
+                float* ms) {
+    int64_t b, len;
+    tune_shape(r, batch, &b, &len);
+    const Step& st = *r.st;
+    if (r.cls >= 0) {
+        k_ragged_uniform<<<blocks_for(b + 1), kThreads, 0, s>>>(tb.offs, tb.list, tb.ctr, b, len);
+        TDH_CUDA(cudaGetLastError());
+    }
+    auto launch = [&]() -> int {
+        if (r.cls < 0) return exec_launch(st, std::is_same<T, float>::value ? TDH_FP32 : TDH_FP64,
+                                          tb.in, tb.out, b, 0, s);
+        TDH_CUDA(cudaMemsetAsync(tb.ctr + 1, 0, sizeof(int), s));
+        const ExecData& ex = st.rcls[r.cls];
+        ExecParams<T> P = ragged_params<T>(st, ex, tb.in, tb.out, tb.offs, tb.list, tb.ctr,
+                                           tb.ctr + 1, b);
+        return dispatch<T>(ex.g, P, b, s);
+    };
+    TDH_TRY(launch());
+    for (int i = 0; i < 4; ++i) {
+        TDH_CUDA(cudaEventRecord(tb.ev[i], s));
+        if (i < 3) TDH_TRY(launch());
+    }
+    TDH_CUDA(cudaEventSynchronize(tb.ev[3]));
+    float best = 0;
+    for (int i = 0; i < 3; ++i) {
+        float t = 0;
+        TDH_CUDA(cudaEventElapsedTime(&t, tb.ev[i], tb.ev[i + 1]));
+        if (i == 0 || t < best) best = t;
+    }
+    *ms = best;
+    return TDH_OK;
+}
+
+template <typename T>
+int autotune_typed(tdh_plan_s& plan, int64_t batch, cudaStream_t s) {
+    const int prec = plan.params.prec;
+    std::vector<ConfigRef> cfgs = plan_configs(plan);
+    int64_t elems = 0, bmax = 0;
+    for (const ConfigRef& r : cfgs) {
+        int64_t b, len;
+        tune_shape(r, batch, &b, &len);
+        elems = std::max(elems, b * len);
+        bmax = std::max(bmax, b);
+    }
+    TuneBuffers tb;
+    int rc = TDH_OK;
+    auto cleanup = [&] {
+        cudaStreamSynchronize(s);
+        for (cudaEvent_t e : tb.ev)
+            if (e) cudaEventDestroy(e);
+        dev_free(tb.in);
+        dev_free(tb.out);
+        dev_free(tb.offs);
+        dev_free(tb.list);
+        dev_free(tb.ctr);
+    };
+    if ((rc = dev_alloc(&tb.in, sizeof(T) * (size_t)elems)) ||
+        (rc = dev_alloc(&tb.out, sizeof(T) * (size_t)elems)) ||
+        (rc = dev_alloc_t(&tb.offs, (size_t)bmax + 1)) ||
+        (rc = dev_alloc_t(&tb.list, (size_t)bmax)) || (rc = dev_alloc_t(&tb.ctr, 2))) {
+        cleanup();
+        return rc;
+    }
+    for (cudaEvent_t& e : tb.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            set_error("autotune: event creation failed");
+            cleanup();
+            return TDH_ERR_CUDA;
+        }
+    k_fill_test<T><<<blocks_for(elems), kThreads, 0, s>>>(static_cast<T*>(tb.in), elems);
+    for (const ConfigRef& r : cfgs) {
+        const std::vector<Geometry> cands =
+            schedule_candidates(prec, config_data(r).g.logL, r.cls >= 0);
+        if (cands.size() < 2) continue;
+        int best = -1;
+        float best_ms = 0;
+        for (size_t i = 0; rc == TDH_OK && i < cands.size(); ++i) {
+            float ms = 0;
+            rc = rebuild_config(r, prec, cands[i], s);
+            if (rc == TDH_OK) rc = time_config<T>(r, batch, tb, s, &ms);
+            if (rc == TDH_OK && (best < 0 || ms < best_ms)) {
+                best = (int)i;
+                best_ms = ms;
+            }
+        }
+        if (rc == TDH_OK) rc = rebuild_config(r, prec, cands[best], s);
+        if (rc != TDH_OK) break;
+    }
+    cleanup();
+    return rc;
+}
+
+}  // namespace
+
+int exec_schedule_count(const tdh_plan_s& plan) {
+    return (int)plan_configs(const_cast<tdh_plan_s&>(plan)).size();
+}
+
+int exec_schedule_info(const tdh_plan_s& plan, int config, int* info) {
+    std::vector<ConfigRef> cfgs = plan_configs(const_cast<tdh_plan_s&>(plan));
+    if (config < 0 || config >= (int)cfgs.size()) {
+        set_error("configuration %d out of range (%d)", config, (int)cfgs.size());
+        return TDH_ERR_INVALID_ARG;
+    }
+    const ConfigRef& r = cfgs[config];
+    const Geometry& g = config_data(r).g;
+    const std::vector<Geometry> cands = schedule_candidates(plan.params.prec, g.logL, r.cls >= 0);
+    int idx = -1;
+    for (size_t i = 0; i < cands.size(); ++i)
+        if (same_schedule(cands[i], g)) idx = (int)i;
+    const int v[8] = {g.logL, g.logLC, g.C, g.R, g.NT, g.MINB, idx, (int)cands.size()};
+    for (int i = 0; i < 8; ++i) info[i] = v[i];
+    return TDH_OK;
+}
+
+int exec_set_schedule(tdh_plan_s& plan, int index, cudaStream_t s) {
+    if (index < 0) {
+        set_error("schedule index must be >= 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    for (const ConfigRef& r : plan_configs(plan)) {
+        const std::vector<Geometry> cands =
+            schedule_candidates(plan.params.prec, config_data(r).g.logL, r.cls >= 0);
+        if (cands.empty()) continue;
+        TDH_TRY(rebuild_config(r, plan.params.prec, cands[std::min<size_t>(index, cands.size() - 1)],
+                               s));
+    }
+    return TDH_OK;
+}
+
+int exec_autotune(tdh_plan_s& plan, int64_t batch, cudaStream_t s) {
+    if (batch < 1) {
+        set_error("autotune batch must be >= 1");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (plan.params.prec == TDH_FP32) return autotune_typed<float>(plan, batch, s);
+    return autotune_typed<double>(plan, batch, s);
 }
 
 }  // namespace tdh

@@ -70,6 +70,42 @@ __host__ __device__ inline int local_freq(const PassGeom& G, int pos) {
     return f;
 }
 
+// Radix of the local passes: 16 where the float32 FFT has room for it, else 8.
+__host__ __device__ constexpr int radix_for(bool f32, int logLC) {
+    return f32 && logLC > 9 ? 16 : 8;
+}
+
+// Compiled execute schedules: local FFT length 2^logLC, cluster size C, threads per CTA NT and
+// the occupancy the registers are capped for (MINB CTAs per SM: 65536 / (NT MINB) registers
+// per thread).  The first schedule of each (logLC, C) is the default one; the others trade
+// threads per CTA for CTAs per SM, or local length for cluster size.
+struct Sched {
+    int logLC, C, NT, MINB;
+};
+constexpr Sched kSchedF32[] = {
+    {8, 1, 32, 1},    {8, 1, 32, 16},   {9, 1, 64, 1},    {9, 1, 64, 8},    {10, 1, 64, 1},
+    {10, 1, 64, 8},   {10, 1, 32, 16},  {11, 1, 128, 1},  {11, 1, 128, 4},  {11, 1, 64, 8},
+    {12, 1, 256, 1},  {12, 1, 256, 2},  {12, 1, 128, 4},  {13, 1, 512, 1},  {13, 1, 256, 2},
+    {14, 1, 512, 1},  {14, 2, 512, 1},  {14, 4, 512, 1},  {14, 8, 512, 1},  {13, 2, 256, 2},
+    {13, 4, 256, 2},  {13, 8, 256, 2},
+};
+constexpr Sched kSchedF64[] = {
+    {8, 1, 32, 1},    {8, 1, 32, 16},   {9, 1, 64, 1},    {9, 1, 64, 8},    {10, 1, 128, 1},
+    {10, 1, 128, 4},  {11, 1, 256, 1},  {11, 1, 256, 2},  {11, 1, 128, 4},  {12, 1, 512, 1},
+    {12, 1, 256, 2},  {13, 1, 512, 1},  {13, 2, 512, 1},  {13, 4, 512, 1},  {13, 8, 512, 1},
+    {12, 2, 256, 2},  {12, 4, 256, 2},  {12, 8, 256, 2},
+};
+template <bool F32>
+struct SchedTable {
+    static constexpr int size = (int)(sizeof(kSchedF32) / sizeof(Sched));
+    static constexpr Sched at(int i) { return kSchedF32[i]; }
+};
+template <>
+struct SchedTable<false> {
+    static constexpr int size = (int)(sizeof(kSchedF64) / sizeof(Sched));
+    static constexpr Sched at(int i) { return kSchedF64[i]; }
+};
+
 template <typename T>
 struct ExecParams {
     using V = typename cx<T>::t;
@@ -542,8 +578,8 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 // Dense batches: cluster blockIdx.x / C converts vector blockIdx.x / C.  Ragged batches
 // (RAGGED): persistent clusters take vectors of one FFT-length class from a work counter.
 // Two kernels so that each inlines the per-vector body once (register pressure).
-template <typename T, int LOGLC, int R, int C, int NT, bool RAGGED>
-__global__ void __launch_bounds__(NT, 1) exec_kernel(const ExecParams<T> P) {
+template <typename T, int LOGLC, int R, int C, int NT, int MINB, bool RAGGED>
+__global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
     constexpr int LC = G.LC();
@@ -623,13 +659,13 @@ __global__ void k_balance_fixup(const T* __restrict__ partial, T* __restrict__ o
     out[v * n + k] = acc;
 }
 
-template <typename T, int LOGLC, int R, int C, int NT, bool RAGGED>
+template <typename T, int LOGLC, int R, int C, int NT, int MINB, bool RAGGED>
 int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
     constexpr size_t smem = (size_t)(padded_len<V>(G.LC()) + G.LC() / 2 + G.twp_len()) * sizeof(V);
     static_assert(smem <= 232448, "shared memory budget");
-    auto kern = exec_kernel<T, LOGLC, R, C, NT, RAGGED>;
+    auto kern = exec_kernel<T, LOGLC, R, C, NT, MINB, RAGGED>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -711,40 +747,24 @@ int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
 }
 
 // Kernel instantiation for a geometry (switch over the built configurations).
-template <typename T, bool RAGGED>
+// Table-driven dispatch: the kernel instantiation whose schedule equals g's.
+template <typename T, bool RAGGED, int I = 0>
 int dispatch_geom(const Geometry& g, const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
-    if constexpr (std::is_same<T, float>::value) {
-        switch (g.logLC * 16 + g.C) {
-        case 8 * 16 + 1: return launch_inst<float, 8, 8, 1, 32, RAGGED>(P, batch, s);
-        case 9 * 16 + 1: return launch_inst<float, 9, 8, 1, 64, RAGGED>(P, batch, s);
-        case 10 * 16 + 1: return launch_inst<float, 10, 16, 1, 64, RAGGED>(P, batch, s);
-        case 11 * 16 + 1: return launch_inst<float, 11, 16, 1, 128, RAGGED>(P, batch, s);
-        case 12 * 16 + 1: return launch_inst<float, 12, 16, 1, 256, RAGGED>(P, batch, s);
-        case 13 * 16 + 1: return launch_inst<float, 13, 16, 1, 512, RAGGED>(P, batch, s);
-        case 14 * 16 + 1: return launch_inst<float, 14, 16, 1, 512, RAGGED>(P, batch, s);
-        case 14 * 16 + 2: return launch_inst<float, 14, 16, 2, 512, RAGGED>(P, batch, s);
-        case 14 * 16 + 4: return launch_inst<float, 14, 16, 4, 512, RAGGED>(P, batch, s);
-        case 14 * 16 + 8: return launch_inst<float, 14, 16, 8, 512, RAGGED>(P, batch, s);
-        }
+    constexpr bool f32 = std::is_same<T, float>::value;
+    if constexpr (I < SchedTable<f32>::size) {
+        constexpr Sched e = SchedTable<f32>::at(I);
+        if (g.logLC == e.logLC && g.C == e.C && g.NT == e.NT && g.MINB == e.MINB)
+            return launch_inst<T, e.logLC, radix_for(f32, e.logLC), e.C, e.NT, e.MINB, RAGGED>(
+                P, batch, s);
+        return dispatch_geom<T, RAGGED, I + 1>(g, P, batch, s);
     } else {
-        switch (g.logLC * 16 + g.C) {
-        case 8 * 16 + 1: return launch_inst<double, 8, 8, 1, 32, RAGGED>(P, batch, s);
-        case 9 * 16 + 1: return launch_inst<double, 9, 8, 1, 64, RAGGED>(P, batch, s);
-        case 10 * 16 + 1: return launch_inst<double, 10, 8, 1, 128, RAGGED>(P, batch, s);
-        case 11 * 16 + 1: return launch_inst<double, 11, 8, 1, 256, RAGGED>(P, batch, s);
-        case 12 * 16 + 1: return launch_inst<double, 12, 8, 1, 512, RAGGED>(P, batch, s);
-        case 13 * 16 + 1: return launch_inst<double, 13, 8, 1, 512, RAGGED>(P, batch, s);
-        case 13 * 16 + 2: return launch_inst<double, 13, 8, 2, 512, RAGGED>(P, batch, s);
-        case 13 * 16 + 4: return launch_inst<double, 13, 8, 4, 512, RAGGED>(P, batch, s);
-        case 13 * 16 + 8: return launch_inst<double, 13, 8, 8, 512, RAGGED>(P, batch, s);
-        }
+        set_error("no %s kernel for local length 2^%d, cluster %d, %d threads, %d CTAs per SM",
+                  f32 ? "float32" : "float64", g.logLC, g.C, g.NT, g.MINB);
+        return TDH_ERR_UNSUPPORTED;
     }
-    set_error("no %s kernel for local length 2^%d, cluster %d",
-              std::is_same<T, float>::value ? "float32" : "float64", g.logLC, g.C);
-    return TDH_ERR_UNSUPPORTED;
 }
 
-// Defined in tdh_exec.cu (dense) and tdh_ragged.cu (ragged), one instantiation set each.
+// Defined in tdh_dense_f32/f64.cu and tdh_ragged_f32/f64.cu, one instantiation set each.
 int dispatch_dense(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s);
 int dispatch_dense(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s);
 int dispatch_ragged(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s);

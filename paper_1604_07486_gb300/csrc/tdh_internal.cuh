@@ -68,6 +68,7 @@ struct Geometry {
     int C;      // cluster size (CTAs per vector)
     int R;      // radix of the local passes
     int NT;     // threads per CTA
+    int MINB;   // CTAs per SM the kernel's registers are capped for (launch bounds)
 };
 
 // Device data of one execute configuration.
@@ -167,6 +168,15 @@ int exec_prepare_ragged(Step& st, int prec, cudaStream_t s);
 int exec_launch_ragged(const Step& st, int prec, const void* in, void* out, const int64_t* offs,
                        int64_t batch, cudaStream_t s, const std::vector<cudaStream_t>& side,
                        const std::vector<cudaEvent_t>& ev);
+// Execute schedules (FFT geometries with a compiled kernel) of the plan's T o H steps.
+// Configurations in order: each T o H step's dense configuration, then (ragged plans) one per
+// FFT length class.  info = {log2 L, log2 LC, C, R, NT, MINB, index, count}.
+int exec_schedule_count(const tdh_plan_s& plan);
+int exec_schedule_info(const tdh_plan_s& plan, int config, int* info);
+// Every configuration takes its schedule min(index, count - 1) (tables rebuilt as needed).
+int exec_set_schedule(tdh_plan_s& plan, int index, cudaStream_t s);
+// Time every schedule of every configuration on synthetic input and keep the fastest.
+int exec_autotune(tdh_plan_s& plan, int64_t batch, cudaStream_t s);
 // Multi-pass execute of one step (FFT longer than one cluster's shared memory).
 int mp_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
               cudaStream_t s);
