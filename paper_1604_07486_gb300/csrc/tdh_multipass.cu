@@ -119,15 +119,15 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_fwd(const MPParams<T
     const int tid = threadIdx.x;
     const int64_t bl = blockIdx.x / P.C;
     const int k1 = blockIdx.x % P.C;
-    for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
     const V* vs = P.vdec + (bl * P.C + k1) * (LC / 2);
     const V* ur = P.u + (r * P.C + k1) * (LC / 2);
-    __syncthreads();
     V zl[J0][R / 2];  // every global load of the pass first: one latency for all groups
 #pragma unroll
     for (int j = 0; j < J0; ++j)
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) zl[j][q] = cwmul(vs[tid + j * NT + q * S0], ur[tid + j * NT + q * S0]);
+    for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];  // overlaps the loads above
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < J0; ++j) {
         const int o = tid + j * NT;
@@ -159,6 +159,19 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_fwd(const MPParams<T
     for (int pos = tid; pos < LC; pos += NT) y[pos] = buf[sidx<V>(pos)];
 }
 
+// Bring `bytes` (a multiple of 16, 16-byte aligned address) into L2 without waiting: one bulk
+// prefetch per 16 KB piece, issued by the first threads of the block.
+__device__ __forceinline__ void prefetch_l2(const void* p, int bytes) {
+    constexpr int kPiece = 16384;
+    const int pieces = (bytes + kPiece - 1) / kPiece;
+    for (int i = threadIdx.x; i < pieces; i += blockDim.x) {
+        const int sz = min(kPiece, bytes - i * kPiece);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                     :: "l"(static_cast<const char*>(p) + (size_t)i * kPiece), "r"(sz)
+                     : "memory");
+    }
+}
+
 template <typename T, int LOGLC, int R, int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T> P, int64_t r) {
     using V = typename cx<T>::t;
@@ -171,16 +184,21 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T
     const int tid = threadIdx.x;
     const int64_t bl = blockIdx.x / P.C;
     const int k1 = blockIdx.x % P.C;
-    for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
+    const V* ur = P.u + (r * P.C + k1) * (LC / 2);
+    V* w = P.W + (bl * P.C + k1) * (LC / 2);
+    // the factor and accumulator slices of the last pass, on their way to L2 meanwhile
+    prefetch_l2(ur, (int)sizeof(V) * (LC / 2));
+    prefetch_l2(w, (int)sizeof(V) * (LC / 2));
     const V* y = P.Y + (bl * P.C + k1) * LC;
-    static_assert(LC % (8 * NT) == 0, "load batches");
-#pragma unroll 1
-    for (int pos0 = tid; pos0 < LC; pos0 += 8 * NT) {
-        V v[8];
+    constexpr int NY = LC / NT;  // the whole slice in one batch of loads
+    static_assert(LC % NT == 0 && NY <= 32, "load batch");
+    {
+        V v[NY];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = y[pos0 + i * NT];
+        for (int i = 0; i < NY; ++i) v[i] = y[tid + i * NT];
+        for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];  // overlaps the loads above
 #pragma unroll
-        for (int i = 0; i < 8; ++i) buf[sidx<V>(pos0 + i * NT)] = v[i];
+        for (int i = 0; i < NY; ++i) buf[sidx<V>(tid + i * NT)] = v[i];
     }
     __syncthreads();
 #pragma unroll 1
@@ -194,8 +212,6 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T
     }
     __syncthreads();
     middle_inv<G.np() - 2, LOGLC, R, NT>(buf, twt);
-    const V* ur = P.u + (r * P.C + k1) * (LC / 2);
-    V* w = P.W + (bl * P.C + k1) * (LC / 2);
 #pragma unroll
     for (int j = 0; j < J0; ++j) {
         const int o = tid + j * NT;
