@@ -44,6 +44,31 @@ struct MPParams {
 
 constexpr int kEw = 256;
 
+// Programmatic dependent launch between the kernels of one multi-pass execute: each kernel
+// lets the next one be scheduled as soon as all of its own CTAs are running, and does only
+// read-only set-up (twiddle tables, plan factors) before it waits for the previous kernel to
+// complete and its writes to be visible.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = a;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename V>
 __device__ __forceinline__ V omega_L(const V* thi, const V* tlo, int64_t e, int64_t L, int shift) {
     e &= (L - 1);
@@ -119,14 +144,20 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_fwd(const MPParams<T
     const int tid = threadIdx.x;
     const int64_t bl = blockIdx.x / P.C;
     const int k1 = blockIdx.x % P.C;
+    pdl_trigger();
     const V* vs = P.vdec + (bl * P.C + k1) * (LC / 2);
     const V* ur = P.u + (r * P.C + k1) * (LC / 2);
     V zl[J0][R / 2];  // every global load of the pass first: one latency for all groups
 #pragma unroll
     for (int j = 0; j < J0; ++j)
 #pragma unroll
-        for (int q = 0; q < R / 2; ++q) zl[j][q] = cwmul(vs[tid + j * NT + q * S0], ur[tid + j * NT + q * S0]);
+        for (int q = 0; q < R / 2; ++q) zl[j][q] = ur[tid + j * NT + q * S0];
     for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];  // overlaps the loads above
+    pdl_wait();  // v was written by an earlier kernel
+#pragma unroll
+    for (int j = 0; j < J0; ++j)
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) zl[j][q] = cwmul(vs[tid + j * NT + q * S0], zl[j][q]);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < J0; ++j) {
@@ -184,10 +215,12 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T
     const int tid = threadIdx.x;
     const int64_t bl = blockIdx.x / P.C;
     const int k1 = blockIdx.x % P.C;
+    pdl_trigger();
     const V* ur = P.u + (r * P.C + k1) * (LC / 2);
     V* w = P.W + (bl * P.C + k1) * (LC / 2);
     // the factor and accumulator slices of the last pass, on their way to L2 meanwhile
     prefetch_l2(ur, (int)sizeof(V) * (LC / 2));
+    pdl_wait();  // Y and W were written by earlier kernels
     prefetch_l2(w, (int)sizeof(V) * (LC / 2));
     const V* y = P.Y + (bl * P.C + k1) * LC;
     constexpr int NY = LC / NT;  // the whole slice in one batch of loads
@@ -257,8 +290,10 @@ __global__ void __launch_bounds__(256) mp_cross(const MPParams<T> P) {
     V* twc = tile + PPB * ld;                  // omega_C^k, k < C/2
     const int64_t bl = blockIdx.y;
     const int pos0 = blockIdx.x * PPB;
+    pdl_trigger();
     for (int k = threadIdx.x; k < C / 2; k += blockDim.x)
         twc[k] = omega_L(P.thi, P.tlo, (int64_t)k * (P.L / C), P.L, P.shift);
+    pdl_wait();  // Y was written by the previous kernel
     const V* Yb = P.Y + bl * (int64_t)C * LC;
     V* Yw = P.Y + bl * (int64_t)C * LC;
     for (int idx = threadIdx.x; idx < PPB * C; idx += blockDim.x) {
@@ -324,8 +359,10 @@ __global__ void __launch_bounds__(256) mp_cross16(const MPParams<T> P) {
     const int tid = threadIdx.x;
     const int64_t bl = blockIdx.y;
     const int pos0 = blockIdx.x * PP;
+    pdl_trigger();
     for (int k = tid; k < C; k += NTH)
         twc[k] = omega_L(P.thi, P.tlo, (int64_t)k * (P.L / C), P.L, P.shift);
+    pdl_wait();  // Y was written by the previous kernel
     V* Yb = P.Y + bl * (int64_t)C * LC;
     // phases A and E: thread (p, k0) moves slices k1 = k0 + C2 i, i < 16, of position p (all
     // loads of a thread independent, so they are in flight together)
@@ -412,7 +449,12 @@ int cross16_launch(const MPParams<T>& Q, int64_t nb, cudaStream_t s) {
         set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(err));
         return TDH_ERR_CUDA;
     }
-    mp_cross16<T, LC, C><<<dim3(LC / PP, (unsigned)nb), 256, smem, s>>>(Q);
+    const cudaError_t e =
+        launch_pdl(mp_cross16<T, LC, C>, dim3(LC / PP, (unsigned)nb), dim3(256), smem, s, Q);
+    if (e != cudaSuccess) {
+        set_error("multi-pass cross stage: %s", cudaGetErrorString(e));
+        return TDH_ERR_CUDA;
+    }
     note_launches(1);
     return TDH_OK;
 }
@@ -426,16 +468,23 @@ int cross_launch(const MPParams<T>& Q, int64_t nb, size_t smem_cross, cudaStream
     case 64: return cross16_launch<T, LC, 64>(Q, nb, s);
     case 128: return cross16_launch<T, LC, 128>(Q, nb, s);
     case 256: return cross16_launch<T, LC, 256>(Q, nb, s);
-    default:
-        mp_cross<T, LC><<<dim3(LC / 16, (unsigned)nb), 256, smem_cross, s>>>(Q);
+    default: {
+        const cudaError_t e =
+            launch_pdl(mp_cross<T, LC>, dim3(LC / 16, (unsigned)nb), dim3(256), smem_cross, s, Q);
+        if (e != cudaSuccess) {
+            set_error("multi-pass cross stage: %s", cudaGetErrorString(e));
+            return TDH_ERR_CUDA;
+        }
         note_launches(1);
         return TDH_OK;
+    }
     }
 }
 
 template <typename T, int LC>
 __global__ void mp_store(const MPParams<T> P, int64_t b0, int64_t nb) {
     using V = typename cx<T>::t;
+    pdl_wait();  // W (and the row-0 sums) were written by earlier kernels
     const int64_t per_out = P.n;
     const int64_t total = nb * per_out;
     for (int64_t i = (int64_t)blockIdx.x * kEw + threadIdx.x; i < total;
@@ -529,18 +578,22 @@ int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjo
         mp_load<T, LC><<<ew, kEw, 0, s>>>(Q, 0, nb);
         if (P.row0) mp_row0<T><<<(unsigned)nb, kEw, 0, s>>>(Q, 0);
         note_launches(P.row0 ? 2 : 1);
-        for (int64_t r = 0; rc == TDH_OK && r < P.K; ++r) {
-            mp_fwd<T, LOGLC, R, NT><<<(unsigned)(nb * P.C), NT, smem_pass, s>>>(Q, r);
+        cudaError_t e = cudaSuccess;
+        const dim3 gp((unsigned)(nb * P.C)), bp(NT);
+        for (int64_t r = 0; rc == TDH_OK && e == cudaSuccess && r < P.K; ++r) {
+            e = launch_pdl(mp_fwd<T, LOGLC, R, NT>, gp, bp, smem_pass, s, Q, r);
+            if (e != cudaSuccess) break;
             rc = cross_launch<T, LC>(Q, nb, smem_cross, s);
-            mp_inv<T, LOGLC, R, NT><<<(unsigned)(nb * P.C), NT, smem_pass, s>>>(Q, r);
-            note_launches(2);
+            if (rc != TDH_OK) break;
+            e = launch_pdl(mp_inv<T, LOGLC, R, NT>, gp, bp, smem_pass, s, Q, r);
+            if (e == cudaSuccess) note_launches(2);
         }
         if (rc != TDH_OK) break;
         Q.in = P.in;
         const unsigned eo = (unsigned)std::min<int64_t>((nb * P.n + kEw - 1) / kEw, 4096);
-        mp_store<T, LC><<<eo, kEw, 0, s>>>(Q, b0, nb);
-        note_launches(1);
-        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_pdl(mp_store<T, LC>, dim3(eo), dim3(kEw), 0, s, Q, b0, nb);
+        if (e == cudaSuccess) note_launches(1);
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) {
             set_error("multi-pass launch: %s", cudaGetErrorString(e));
             rc = TDH_ERR_CUDA;
