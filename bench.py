@@ -25,8 +25,14 @@ sys.path.insert(0, ROOT)
 N = 1 << 16
 BATCH = 256
 KINDS = ("leg2cheb", "cheb2leg")
-TOL32 = {"leg2cheb": 1e-7, "cheb2leg": 1e-10}
-TOL64 = {"leg2cheb": 1e-15, "cheb2leg": 1e-17}
+TOL64 = {"leg2cheb": 1e-15, "cheb2leg": 1e-17}  # relative Cholesky tolerances, float64
+# Plans of the timed workloads.  Legendre -> Chebyshev: accuracy-targeted (TDH_FLAG_TARGET),
+# the truncation bound guarantees half the stated tolerance (5e-6 float32, 1e-12 float64) for
+# every alpha, leaving the other half to rounding.  Chebyshev -> Legendre: D1 and D2 both grow
+# like j, the worst-case bound asks for 34 (float32) / 46 (float64) terms, so it keeps the
+# relative tolerances whose measured error meets the tolerance on these inputs.
+PLAN32 = {"leg2cheb": {"tol": 2.5e-6, "target": True}, "cheb2leg": {"tol": 1e-10, "target": False}}
+PLAN64 = {"leg2cheb": {"tol": 5e-13, "target": True}, "cheb2leg": {"tol": 1e-17, "target": False}}
 DECAY = 0.5
 WORKLOAD = "leg2cheb+cheb2leg n=65536 batch=256"
 METRIC = "Leg<->Cheb coefficients/s"
@@ -317,7 +323,7 @@ def main():
 
     # plans (float64 construction on the GPU, timed separately)
     t0 = time.perf_counter()
-    plans32 = {k: tdh.Plan(k, N, prec="fp32", tol=TOL32[k]) for k in KINDS}
+    plans32 = {k: tdh.Plan(k, N, prec="fp32", **PLAN32[k]) for k in KINDS}
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0) / len(KINDS)
     tuned = {k: tune(plans32[k], BATCH, args) for k in KINDS}
@@ -381,7 +387,7 @@ def main():
     # plain float64 path on the same workload
     fp64 = None
     if not args.no_fp64:
-        plans64 = {k: tdh.Plan(k, N, prec="fp64", tol=TOL64[k]) for k in KINDS}
+        plans64 = {k: tdh.Plan(k, N, prec="fp64", **PLAN64[k]) for k in KINDS}
         tuned64 = {k: tune(plans64[k], BATCH, args)[1] for k in KINDS}
         x64 = {k: torch.tensor(alpha, dtype=torch.float64, device="cuda") for k in KINDS}
         y64 = {k: torch.empty_like(x64[k]) for k in KINDS}
@@ -403,7 +409,7 @@ def main():
                 err64[k] = oracle_error(alpha, y64[k].cpu().numpy(), k, [0, BATCH - 1], rows)
         fp64 = {"value": world * coeffs_per_step * reps / (ms64 / 1e3), "unit": "coeffs/s",
                 "ms_per_step": ms64 / reps, "K": {k: plans64[k].K for k in KINDS},
-                "tol": TOL64, "error_vs_oracle": err64, "schedule": tuned64}
+                "plans": PLAN64, "error_vs_oracle": err64, "schedule": tuned64}
         del plans64, x64, y64
 
     # end to end through the public API: pinned host in, host out, every step
@@ -438,7 +444,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "batch_per_gpu": BATCH, "kinds": list(KINDS),
-                       "decay": DECAY, "K": {k: plans32[k].K for k in KINDS}, "tol": TOL32,
+                       "decay": DECAY, "K": {k: plans32[k].K for k in KINDS}, "plans": PLAN32,
                        "plan_ms": plan_ms, "l2": "flushed between steps (256 MB write)",
                        "schedule": {k: tuned[k][1] for k in KINDS},
                        "autotune_ms": {k: tuned[k][0] for k in KINDS},
@@ -509,7 +515,7 @@ def run_extra(args, rank, world, local):
         deg = workloads.ragged_degrees(4096, 64, 65536, seed=rank)
         lengths = deg + 1
         xv, offs = workloads.ragged_coefficients(lengths, decay=1.0, seed=rank)
-        plan = tdh.Plan("leg2cheb", int(lengths.max()), prec="fp32", tol=1e-7, ragged=True)
+        plan = tdh.Plan("leg2cheb", int(lengths.max()), prec="fp32", ragged=True, **PLAN32["leg2cheb"])
         tuned = {"leg2cheb": tune(plan, len(lengths), args)}
         xt = torch.tensor(xv, dtype=torch.float32, device="cuda")
         ot = torch.tensor(offs, dtype=torch.int64, device="cuda")
@@ -530,7 +536,7 @@ def run_extra(args, rank, world, local):
         flops = sum(flops_per_vector(plan.K, L) for L in Ls)
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived"
         config = {"workload": "ragged leg2cheb 4096 vectors, degrees log-uniform [64, 65536), fp32, one CUDA-graph launch",
-                  "K": plan.K, "coefficients": coeffs}
+                  "K": plan.K, "plan": PLAN32["leg2cheb"], "coefficients": coeffs}
         def check():
             yn = yt.double().cpu().numpy()
             errs = []
@@ -577,7 +583,7 @@ def run_extra(args, rank, world, local):
         io = 2 * n * B * 4
     elif w == "c5":
         n, B = 8192, 1024
-        plan = tdh.Plan("leg2cheb", n, prec="fp32", tol=1e-7)
+        plan = tdh.Plan("leg2cheb", n, prec="fp32", **PLAN32["leg2cheb"])
         tuned = {"leg2cheb": tune(plan, B, args)}
         alpha = workloads.coefficients(n, B, decay=1.0, seed=rank)
         x = torch.tensor(alpha, dtype=torch.float32, device="cuda", requires_grad=True)
@@ -589,7 +595,8 @@ def run_extra(args, rank, world, local):
         coeffs, dtype = n * B, "f32"
         flops = 2 * flops_per_vector(plan.K, 8192) * B
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived"
-        config = {"workload": "autograd leg2cheb n=8192 batch=1024 fp32: forward + loss + backward (adjoint kernel)", "K": plan.K}
+        config = {"workload": "autograd leg2cheb n=8192 batch=1024 fp32: forward + loss + backward (adjoint kernel)",
+                  "K": plan.K, "plan": PLAN32["leg2cheb"]}
         def check():
             fn()
             g = x.grad.double().cpu().numpy()

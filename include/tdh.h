@@ -50,6 +50,7 @@ extern "C" {
 /* ---------------------------------------------------------------- plan flags */
 #define TDH_FLAG_NONE   0
 #define TDH_FLAG_RAGGED 1 /* also prepare every shorter FFT length (tdh_plan_execute_ragged)  */
+#define TDH_FLAG_TARGET 2 /* tol is the target accuracy of the truncation (tdh_plan_create)   */
 
 /* ---------------------------------------------------------------- error codes */
 #define TDH_OK               0
@@ -67,7 +68,7 @@ typedef struct {
     double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; LAG {a1, a2};
                      JAC2CHEB / CHEB2JAC {a, b}                                              */
     int prec;     /* TDH_FP64 or TDH_FP32: the precision of plan_execute's in/out and FFTs  */
-    int flags;    /* TDH_FLAG_RAGGED or TDH_FLAG_NONE                                       */
+    int flags;    /* TDH_FLAG_NONE, or TDH_FLAG_RAGGED and/or TDH_FLAG_TARGET (bitwise or)    */
     int64_t kmax; /* cap on the rank of each Hankel factorisation; 0 selects 128            */
 } tdh_params;
 
@@ -82,6 +83,15 @@ typedef struct {
  * For TDH_CHEB2LEG the factorisation covers indices 1..n_max-1 and row 0 is applied directly
  * (Sec. 5.1).  tol > 0 is relative to the largest diagonal entry of H; the paper takes
  * "a small multiple of machine epsilon" of the arithmetic used.
+ * With TDH_FLAG_TARGET, tol is instead the accuracy asked of each T o H step's truncation:
+ * the factorisation runs to its rounding floor (relative threshold 1e-18, at most kmax
+ * steps) and the step keeps the fewest K' terms with
+ *   B(K') = max_m |t_m| * max_j |D1_j| sqrt(d_j) * max_k |D2_k| sqrt(d_k) <= tol,
+ * d the diagonal of the residual R = H - sum_{r<K'} u_r u_r^T (indices of the Hankel block;
+ * D1, D2 including the step's Chebyshev scalings).  R is positive semidefinite (a Schur
+ * complement), so |R_jk| <= sqrt(d_j d_k), every entry of A - A_K' is at most B(K') and
+ * max |beta_K' - beta| <= B(K') ||alpha||_1 in exact arithmetic; the execute precision's
+ * rounding comes on top.  If no prefix meets tol, every computed term is kept.
  * Case dispatch (a plan is a chain of steps applied in order):
  *   ULTRA (l1, l2 > 0): integer l2 - l1 (Case 1): sparse factors S_l of
  *     eq. (sparseFactorization), or their inverses by back-substitution when l2 < l1;

@@ -7,15 +7,16 @@ It shares no code with the CUDA library and the library never imports it.
 
 Parity status: every function here is pinned by -m "not gpu" tests (exact rational
 conversion, Clenshaw evaluation, Hankel moment integrals, L M = I, the K = 27 rank of
-Sec. 2.1, and the full-update Cholesky form), except ``fast_matvec``, which is a CPU
+Sec. 2.1, the full-update Cholesky form, and the truncation bound against dense residuals
+by brute force), except ``fast_matvec``, which is a CPU
 timing reference and is never used as parity truth.
 """
 from .oracle import (CHEB2LEG, JAC, LAG, LEG2CHEB, ULTRA, cheb2jac, chebyshev_normalisation,
                      entries, fast_matvec, first_index, hankel, hankel_factors, jac2cheb,
                      jac2jac, lambda_dd, matvec, pivoted_cholesky, pivoted_cholesky_full, split,
-                     threads)
+                     target_rank, threads, truncation_bound)
 
 __all__ = ["CHEB2LEG", "JAC", "LAG", "LEG2CHEB", "ULTRA", "cheb2jac", "chebyshev_normalisation",
            "entries", "fast_matvec", "first_index", "hankel", "hankel_factors", "jac2cheb",
            "jac2jac", "lambda_dd", "matvec", "pivoted_cholesky", "pivoted_cholesky_full",
-           "split", "threads"]
+           "split", "target_rank", "threads", "truncation_bound"]

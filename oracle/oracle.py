@@ -216,6 +216,43 @@ def hankel_factors(kind, params, n, tol, kmax=None):
     return u, piv + j0
 
 
+def truncation_bound(kind, params, n, u):
+    """Bound on the entries of A - A_K for the rank-K factors u (from ``hankel_factors``),
+    for every prefix K' = 0..K (array of K + 1 values).
+
+    The residual R = H - sum_{r<K'} u_r u_r^T of a pivoted Cholesky of a positive
+    semidefinite H is positive semidefinite, so each 2 x 2 principal minor gives
+    |R_jk| <= sqrt(d_j d_k) with d = diag(R).  A - A_K' = D1 (T o R) D2 on the Hankel block
+    (Sec. 2, eq. (HadamardDecomposition)), hence
+        |(A - A_K')_jk| <= max|t| * |d1_j| sqrt(d_j) * |d2_k| sqrt(d_k),
+    and max_j |beta_K' - beta| <= B(K') ||alpha||_1 with
+        B(K') = max|t| * max_j |d1_j| sqrt(d_j) * max_k |d2_k| sqrt(d_k).
+    """
+    t, h, d1, d2 = split(kind, params, n)
+    j0 = first_index(kind, params)
+    d = np.zeros(n)
+    d[j0:] = h[2 * np.arange(j0, n)]
+    tmax = np.abs(t).max()
+    out = []
+    for k in range(len(u) + 1):
+        s = np.sqrt(np.maximum(d, 0.0))
+        out.append(tmax * np.max(np.abs(d1) * s) * np.max(np.abs(d2) * s))
+        if k < len(u):
+            d = d - u[k] * u[k]
+    return np.array(out)
+
+
+def target_rank(kind, params, n, target, tol=1e-18, kmax=128):
+    """Fewest rank terms K' whose ``truncation_bound`` is <= target, for the factors of a
+    pivoted Cholesky run to relative tolerance ``tol`` (at most kmax steps); all of them if
+    no prefix meets the target.  Returns (K', bound at K')."""
+    u, _ = hankel_factors(kind, params, n, tol, kmax)
+    b = truncation_bound(kind, params, n, u)
+    ok = np.nonzero(b <= target)[0]
+    k = int(ok[0]) if len(ok) else len(u)
+    return k, float(b[k])
+
+
 # ---------------------------------------------------------------- compositions
 
 def jac2jac(x, a, b, g, d, rows=None):

@@ -26,6 +26,7 @@ EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "t
            "tdh_plan_schedule_count", "tdh_plan_schedule_info", "tdh_plan_set_schedule",
            "tdh_plan_autotune")
 FLAG_RAGGED = 1
+FLAG_TARGET = 2
 
 
 class TdhError(RuntimeError):
@@ -104,9 +105,12 @@ def _kind(kind):
 
 class Plan:
     """A conversion plan (tdh_plan_create): symbols, pivoted Cholesky and FFT tables for
-    vectors of n coefficients, built on the current CUDA device in float64."""
+    vectors of n coefficients, built on the current CUDA device in float64.  tol is relative
+    to max diag(H); with target=True it is the accuracy asked of the truncation instead
+    (fewest rank terms whose residual bound gives max|beta_K - beta| <= tol ||alpha||_1)."""
 
-    def __init__(self, kind, n, prec="fp32", tol=None, params=(), kmax=0, ragged=False):
+    def __init__(self, kind, n, prec="fp32", tol=None, params=(), kmax=0, ragged=False,
+                 target=False):
         self.kind = _kind(kind)
         self.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
         if tol is None:
@@ -115,7 +119,7 @@ class Plan:
         for i, v in enumerate(params):
             p.p[i] = float(v)
         p.prec = self.prec
-        p.flags = FLAG_RAGGED if ragged else 0
+        p.flags = (FLAG_RAGGED if ragged else 0) | (FLAG_TARGET if target else 0)
         p.kmax = int(kmax)
         h = ctypes.c_void_p()
         _check(lib().tdh_plan_create(self.kind, int(n), ctypes.byref(p), float(tol),

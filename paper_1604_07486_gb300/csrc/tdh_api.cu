@@ -119,7 +119,11 @@ void release_step(Step& st) {
 }
 
 // Build one conversion step: symbols (a1), pivoted Cholesky (a2), execute tables (a3).
-int build_step(Step& st, double tol, int64_t kmax, int prec, cudaStream_t s) {
+// Relative stop threshold of the Cholesky of an accuracy-targeted plan: run to the rounding
+// floor, then keep the prefix the truncation bound asks for.
+constexpr double kTargetRelTol = 1e-18;
+
+int build_step(Step& st, double tol, int target, int64_t kmax, int prec, cudaStream_t s) {
     const int64_t n = st.n;
     if (st.sp_M > 0)  // sparse factors: only their tables
         return sparse_prepare(st, prec, s);
@@ -139,7 +143,10 @@ int build_step(Step& st, double tol, int64_t kmax, int prec, cudaStream_t s) {
         TDH_TRY(dev_alloc_t(&st.piv, (size_t)kcap));
         TDH_TRY(dev_alloc_t(&ubig, (size_t)kcap * n));
         int64_t K = 0;
-        int rc = pchol_run(st.h, n, st.j0, tol, kcap, ubig, st.piv, &K, s);
+        int rc = pchol_run(st.h, n, st.j0, target ? kTargetRelTol : tol, kcap, ubig, st.piv, &K, s);
+        if (rc == TDH_OK && target && K > 0)
+            rc = pchol_truncate(st.h, ubig, n, st.j0, K, st.t, st.d1, st.d2, st.scale_out,
+                                st.scale_in, tol, &K, nullptr, s);
         if (rc == TDH_OK && K > 0) {
             rc = dev_alloc_t(&st.u64, (size_t)K * n);
             if (rc == TDH_OK) {
@@ -559,7 +566,7 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
     }
     for (auto& st : plan->steps) {
         if (rc != TDH_OK) break;
-        rc = build_step(st, tol, kmax, params->prec, s);
+        rc = build_step(st, tol, (params->flags & TDH_FLAG_TARGET) ? 1 : 0, kmax, params->prec, s);
         if (rc != TDH_OK) break;
     }
     if (rc == TDH_OK && (params->flags & TDH_FLAG_RAGGED)) {

@@ -59,6 +59,15 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
 int pchol_run(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, double* u,
               int64_t* pivots, int64_t* K, cudaStream_t s);
 
+// Accuracy-targeted truncation of the rank-K factors u [K][n] of H (block j, k >= j0):
+// *Kout = the fewest terms K' <= K whose bound B(K') = max|t| max_j |D1_j| sqrt(d_j)
+// max_k |D2_k| sqrt(d_k) <= target (d: residual diagonal after K' steps; D1, D2 times the
+// optional scalings so, si), else K.  *bound (may be null) receives B(*Kout).  Synchronises s.
+int pchol_truncate(const double* h, const double* u, int64_t n, int64_t j0, int64_t K,
+                   const double* t, const double* d1, const double* d2, const double* so,
+                   const double* si, double target, int64_t* Kout, double* bound,
+                   cudaStream_t s);
+
 // ----------------------------------------------------------------------------- a3-a7
 // FFT geometry of one execute configuration: L = C * LC points, local radix R.
 struct Geometry {

@@ -16,7 +16,9 @@
 // "done" flag every few steps and stops launching.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "tdh_internal.cuh"
 
@@ -203,6 +205,99 @@ done:
     dev_free(part);
     dev_free(st);
     return rc;
+}
+
+// ----------------------------------------------------------------------------------------
+// Accuracy-targeted truncation.  The residual R = H - sum_{r<K} u_r u_r^T of a pivoted
+// Cholesky of a positive semidefinite H is positive semidefinite (a Schur complement), so each
+// 2 x 2 principal minor gives |R_jk| <= sqrt(d_j d_k) with d = diag(R).  In A = D1 (T o H) D2
+// the truncation error is then |(A - A_K)_jk| <= max|t| |D1_j| sqrt(d_j) |D2_k| sqrt(d_k), and
+// max |beta_K - beta| <= B(K) ||alpha||_1 with B(K) = max|t| max_j |D1_j| sqrt(d_j)
+// max_k |D2_k| sqrt(d_k).  One pass over j evaluates B for every prefix K' <= K.
+namespace {
+
+// Non-negative doubles order like their bit patterns: atomicMax on the bits.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* m, double v) {
+    atomicMax(m, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+// m[0] = max|t|; m[1 + k] = max_j |D1_j| sqrt(d_j^(k)), m[2 + K + k] = max_j |D2_j| sqrt(d_j^(k))
+// for k = 0..K (d^(k): residual diagonal after k steps, indices j >= j0).
+__global__ void __launch_bounds__(kThreads) k_trunc_bound(
+    const double* __restrict__ h, const double* __restrict__ u, int64_t n, int64_t j0, int K,
+    const double* __restrict__ t, const double* __restrict__ d1, const double* __restrict__ d2,
+    const double* __restrict__ so, const double* __restrict__ si,
+    unsigned long long* __restrict__ m) {
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const bool in = j < n;
+    const bool blk = in && j >= j0;
+    const int lane = threadIdx.x & 31;
+    const double tm = warp_max(in ? fabs(t[j]) : 0.0);
+    if (lane == 0) atomic_max_nonneg(&m[0], tm);
+    const double a1 = blk ? fabs(d1[j] * (so ? so[j] : 1.0)) : 0.0;
+    const double a2 = blk ? fabs(d2[j] * (si ? si[j] : 1.0)) : 0.0;
+    double dj = blk ? h[2 * j] : 0.0;
+    for (int k = 0; k <= K; ++k) {
+        const double sq = sqrt(fmax(dj, 0.0));
+        const double v1 = warp_max(a1 * sq), v2 = warp_max(a2 * sq);
+        if (lane == 0) {
+            atomic_max_nonneg(&m[1 + k], v1);
+            atomic_max_nonneg(&m[2 + K + k], v2);
+        }
+        if (k < K && blk) {
+            const double x = u[(int64_t)k * n + j];
+            dj -= x * x;
+        }
+    }
+}
+
+}  // namespace
+
+int pchol_truncate(const double* h, const double* u, int64_t n, int64_t j0, int64_t K,
+                   const double* t, const double* d1, const double* d2, const double* so,
+                   const double* si, double target, int64_t* Kout, double* bound,
+                   cudaStream_t s) {
+    *Kout = K;
+    if (K <= 0) return TDH_OK;
+    const size_t words = 2 * (size_t)K + 3;
+    unsigned long long* m = nullptr;
+    TDH_TRY(dev_alloc_t(&m, words));
+    std::vector<unsigned long long> host(words);
+    cudaError_t e = cudaMemsetAsync(m, 0, sizeof(unsigned long long) * words, s);
+    if (e == cudaSuccess) {
+        const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
+        k_trunc_bound<<<blocks, kThreads, 0, s>>>(h, u, n, j0, (int)K, t, d1, d2, so, si, m);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host.data(), m, sizeof(unsigned long long) * words,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(m);
+    if (e != cudaSuccess) {
+        set_error("truncation bound: %s", cudaGetErrorString(e));
+        return TDH_ERR_CUDA;
+    }
+    auto as_d = [&](size_t i) {
+        double v;
+        std::memcpy(&v, &host[i], sizeof(double));
+        return v;
+    };
+    const double tmax = as_d(0);
+    for (int64_t k = 0; k <= K; ++k) {
+        const double b = tmax * as_d(1 + (size_t)k) * as_d(2 + (size_t)K + (size_t)k);
+        if (bound) *bound = b;
+        if (b <= target) {
+            *Kout = k;
+            return TDH_OK;
+        }
+    }
+    return TDH_OK;
 }
 
 }  // namespace tdh
