@@ -87,13 +87,15 @@ constexpr Sched kSchedF32[] = {
     {10, 1, 64, 8},   {10, 1, 32, 16},  {11, 1, 128, 1},  {11, 1, 128, 4},  {11, 1, 64, 8},
     {12, 1, 256, 1},  {12, 1, 256, 2},  {12, 1, 128, 4},  {13, 1, 512, 1},  {13, 1, 256, 2},
     {14, 1, 512, 1},  {14, 2, 512, 1},  {14, 4, 512, 1},  {14, 8, 512, 1},  {13, 2, 256, 2},
-    {13, 4, 256, 2},  {13, 8, 256, 2},
+    {13, 4, 256, 2},  {13, 8, 256, 2},  {9, 2, 64, 1},    {8, 4, 32, 1},    {10, 2, 64, 1},
+    {11, 2, 128, 1},  {12, 2, 256, 2},
 };
 constexpr Sched kSchedF64[] = {
     {8, 1, 32, 1},    {8, 1, 32, 16},   {9, 1, 64, 1},    {9, 1, 64, 8},    {10, 1, 128, 1},
     {10, 1, 128, 4},  {11, 1, 256, 1},  {11, 1, 256, 2},  {11, 1, 128, 4},  {12, 1, 512, 1},
     {12, 1, 256, 2},  {13, 1, 512, 1},  {13, 2, 512, 1},  {13, 4, 512, 1},  {13, 8, 512, 1},
-    {12, 2, 256, 2},  {12, 4, 256, 2},  {12, 8, 256, 2},
+    {12, 2, 256, 2},  {12, 4, 256, 2},  {12, 8, 256, 2},  {9, 2, 64, 1},    {8, 4, 32, 1},
+    {10, 2, 128, 1},  {9, 4, 64, 1},    {11, 2, 256, 1},  {10, 4, 128, 1},
 };
 template <bool F32>
 struct SchedTable {
