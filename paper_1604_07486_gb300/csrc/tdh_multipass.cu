@@ -356,6 +356,10 @@ __global__ void __launch_bounds__(256) mp_cross16(const MPParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* tile = reinterpret_cast<V*>(smem_raw);  // [PP][LD]
     V* twc = tile + PP * LD;                   // omega_C^k, k < C
+    // float64: the phase-A twiddles kept for phase E ([PP][LD]); float32 recomputes them
+    // (measured: keeping them costs float32 more in occupancy than the table loads it saves)
+    constexpr bool kKeepW = sizeof(T) == 8;
+    V* wt = twc + C;
     const int tid = threadIdx.x;
     const int64_t bl = blockIdx.y;
     const int pos0 = blockIdx.x * PP;
@@ -377,7 +381,10 @@ __global__ void __launch_bounds__(256) mp_cross16(const MPParams<T> P) {
             w[i] = omega_L(P.thi, P.tlo, (int64_t)k1 * fpos, P.L, P.shift);
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) tile[pB * LD + aB + C2 * i] = cmul(y[i], w[i]);
+        for (int i = 0; i < 16; ++i) {
+            tile[pB * LD + aB + C2 * i] = cmul(y[i], w[i]);
+            if constexpr (kKeepW) wt[pB * LD + aB + C2 * i] = w[i];
+        }
     }
     __syncthreads();
     // phases B and D: one (position, a) per thread
@@ -421,7 +428,13 @@ __global__ void __launch_bounds__(256) mp_cross16(const MPParams<T> P) {
         for (int b = 0; b < 16; ++b) tile[pB * LD + aB + C2 * b] = x[b];
     }
     __syncthreads();
-    {
+    if constexpr (kKeepW) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int k1 = aB + C2 * i;
+            Yb[(int64_t)k1 * LC + pos0 + pB] = cmulc(tile[pB * LD + k1], wt[pB * LD + k1]);
+        }
+    } else {
         V w[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i)
@@ -438,7 +451,7 @@ template <typename T, int LC, int C>
 int cross16_launch(const MPParams<T>& Q, int64_t nb, cudaStream_t s) {
     using V = typename cx<T>::t;
     constexpr int PP = 4096 / C;
-    constexpr size_t smem = (size_t)(PP * (C + 1) + C) * sizeof(V);
+    constexpr size_t smem = (size_t)((sizeof(T) == 8 ? 2 : 1) * PP * (C + 1) + C) * sizeof(V);
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [&] {
