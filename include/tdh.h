@@ -141,7 +141,8 @@ int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, 
  * one thread-block cluster.  Vectors are grouped by FFT length on the device; each length
  * class is converted by one persistent launch that takes vectors from a work counter, and the
  * classes run concurrently on plan-owned streams forked from `stream` (capturable in a CUDA
- * graph).  Asynchronous; scratch is stream-ordered (see Scratch above).
+ * graph).  Calls from several host threads are serialised while they enqueue (the fork and
+ * join events are the plan's).  Asynchronous; scratch is stream-ordered (see Scratch above).
  */
 int tdh_plan_execute_ragged(tdh_plan_t plan, const void* in, void* out, const int64_t* offsets,
                             int64_t batch, void* stream);

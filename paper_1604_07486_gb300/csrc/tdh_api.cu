@@ -638,6 +638,7 @@ int tdh_plan_execute_ragged(tdh_plan_t plan, const void* in, void* out, const in
         set_error("ragged batch above 2^31 vectors");
         return TDH_ERR_UNSUPPORTED;
     }
+    std::lock_guard<std::mutex> lock(plan->ragged_mu);
     return exec_launch_ragged(plan->steps[0], plan->params.prec, in, out, offsets, batch,
                               as_stream(stream), plan->side, plan->ev);
 }

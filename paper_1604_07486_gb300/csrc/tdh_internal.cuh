@@ -156,6 +156,9 @@ struct tdh_plan_s {
     cudaStream_t hs[2] = {nullptr, nullptr};
     cudaEvent_t hev[7] = {};
     std::mutex host_mu;
+    // serialises the enqueue of ragged calls: their fork/join events are the plan's own, so
+    // each call's records and waits must not interleave with another call's
+    std::mutex ragged_mu;
 };
 
 namespace tdh {
