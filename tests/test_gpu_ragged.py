@@ -98,3 +98,39 @@ def test_ragged_requires_flag(tdh):
     with pytest.raises(tdh.TdhError) as e:
         plan.execute_ragged(x, offs)
     assert e.value.code == -1
+
+
+def test_ragged_concurrent_threads(tdh):
+    """Two host threads convert ragged batches with one plan on two streams at once: the
+    plan's fork/join events are taken in turn, and each result equals the one-thread result."""
+    import threading
+    import torch
+    lengths = workloads.ragged_degrees(300, 16, 20000, seed=8) + 1
+    x, offs = workloads.ragged_coefficients(lengths, decay=1.0, seed=9)
+    plan = tdh.Plan("leg2cheb", int(lengths.max()), prec="fp32", tol=1e-7, ragged=True)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    ot = torch.tensor(offs, dtype=torch.int64, device="cuda")
+    want = plan.execute_ragged(xt, ot)
+    torch.cuda.synchronize()
+    outs, errs = [None, None], []
+
+    def work(i):
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                o = torch.empty_like(xt)
+                for _ in range(20):
+                    plan.execute_ragged(xt, ot, out=o, stream=s)
+            s.synchronize()
+            outs[i] = o
+        except Exception as e:  # reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for o in outs:
+        assert torch.equal(o, want)
