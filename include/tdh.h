@@ -62,7 +62,8 @@ extern "C" {
 #define TDH_ERR_CUDA        (-6) /* a CUDA runtime call failed (message has the detail)     */
 #define TDH_ERR_ALIAS       (-7) /* out overlaps in where the operation forbids it          */
 
-typedef struct tdh_plan_s* tdh_plan_t; /* opaque; immutable after creation */
+/* opaque; after creation only tdh_plan_set_schedule and tdh_plan_autotune change it */
+typedef struct tdh_plan_s* tdh_plan_t;
 
 typedef struct {
     double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; LAG {a1, a2};
