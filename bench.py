@@ -26,15 +26,13 @@ N = 1 << 16
 BATCH = 256
 KINDS = ("leg2cheb", "cheb2leg")
 TOL64 = {"leg2cheb": 1e-15, "cheb2leg": 1e-17}  # relative Cholesky tolerances, float64
-# Plans of the timed workloads.  Legendre -> Chebyshev: accuracy-targeted (TDH_FLAG_TARGET),
-# the truncation bound guarantees half the stated tolerance (5e-6 float32, 1e-12 float64) for
-# every alpha, leaving the other half to rounding.  Chebyshev -> Legendre: D1 and D2 both grow
-# like j, the worst-case bound asks for 34 (float32) / 46 (float64) terms, so it keeps the
-# relative tolerances whose measured error meets the tolerance on these inputs.
-PLAN32 = {"leg2cheb": {"tol": 2.5e-6, "target": True}, "cheb2leg": {"tol": 1e-10, "target": False}}
+# Plans of the timed workloads: accuracy-targeted (TDH_FLAG_TARGET).  The truncation bound
+# guarantees half the stated tolerance (5e-6 float32, 1e-12 float64) for every alpha,
+# leaving the other half to rounding.
+PLAN32 = {"leg2cheb": {"tol": 2.5e-6, "target": True}, "cheb2leg": {"tol": 2.5e-6, "target": True}}
+PLAN64 = {"leg2cheb": {"tol": 5e-13, "target": True}, "cheb2leg": {"tol": 5e-13, "target": True}}
 GUARANTEE = {"leg2cheb": "tolerance met for every alpha (truncation bound)",
-             "cheb2leg": "tolerance met on this workload's inputs (measured); not for every alpha"}
-PLAN64 = {"leg2cheb": {"tol": 5e-13, "target": True}, "cheb2leg": {"tol": 1e-17, "target": False}}
+             "cheb2leg": "tolerance met for every alpha (truncation bound)"}
 DECAY = 0.5
 WORKLOAD = "leg2cheb+cheb2leg n=65536 batch=256"
 METRIC = "Leg<->Cheb coefficients/s"

@@ -85,8 +85,10 @@ typedef struct {
  * (Sec. 5.1).  tol > 0 is relative to the largest diagonal entry of H; the paper takes
  * "a small multiple of machine epsilon" of the arithmetic used.
  * With TDH_FLAG_TARGET, tol is instead the accuracy asked of each T o H step's truncation:
- * the factorisation runs to its rounding floor (relative threshold 1e-18, at most kmax
- * steps) and the step keeps the fewest K' terms with
+ * the factorisation pivots on the congruent W H W, w_j = sqrt(|D1_j D2_j|) (1 where zero;
+ * the same A = D1 W^-1 (T o W H W) W^-1 D2, so the greedy pivot chases the residual that the
+ * output error weighs; its factors are returned divided by w), runs to its rounding floor
+ * (relative threshold 1e-18, at most kmax steps), and the step keeps the fewest K' terms with
  *   B(K') = max_m |t_m| * max_j |D1_j| sqrt(d_j) * max_k |D2_k| sqrt(d_k) <= tol,
  * d the diagonal of the residual R = H - sum_{r<K'} u_r u_r^T (indices of the Hankel block;
  * D1, D2 including the step's Chebyshev scalings).  R is positive semidefinite (a Schur

@@ -13,10 +13,10 @@ timing reference and is never used as parity truth.
 """
 from .oracle import (CHEB2LEG, JAC, LAG, LEG2CHEB, ULTRA, cheb2jac, chebyshev_normalisation,
                      entries, fast_matvec, first_index, hankel, hankel_factors, jac2cheb,
-                     jac2jac, lambda_dd, matvec, pivoted_cholesky, pivoted_cholesky_full, split,
-                     target_rank, threads, truncation_bound)
+                     jac2jac, lambda_dd, matvec, pivot_weights, pivoted_cholesky,
+                     pivoted_cholesky_full, split, target_rank, threads, truncation_bound)
 
 __all__ = ["CHEB2LEG", "JAC", "LAG", "LEG2CHEB", "ULTRA", "cheb2jac", "chebyshev_normalisation",
            "entries", "fast_matvec", "first_index", "hankel", "hankel_factors", "jac2cheb",
-           "jac2jac", "lambda_dd", "matvec", "pivoted_cholesky", "pivoted_cholesky_full",
+           "jac2jac", "lambda_dd", "matvec", "pivot_weights", "pivoted_cholesky", "pivoted_cholesky_full",
            "split", "target_rank", "threads", "truncation_bound"]

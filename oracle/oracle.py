@@ -200,19 +200,33 @@ def pivoted_cholesky_full(H, tol, kmax=None):
     return np.array(ells).reshape(len(ells), N), np.array(a), np.array(piv, dtype=np.int64)
 
 
-def hankel_factors(kind, params, n, tol, kmax=None):
+def pivot_weights(kind, params, n):
+    """w_j = sqrt(|d1_j d2_j|) (1 where that is 0): the diagonal W of the congruence W H W
+    on which an accuracy-targeted factorisation pivots.  W H W is positive semidefinite when
+    H is, and A = D1 (T o H) D2 = (D1 W^-1) (T o W H W) (W^-1 D2)."""
+    _, _, d1, d2 = split(kind, params, n)
+    w = np.sqrt(np.abs(d1 * d2))
+    w[~((w > 0) & np.isfinite(w))] = 1.0
+    return w
+
+
+def hankel_factors(kind, params, n, tol, kmax=None, weights=None):
     """Pivoted Cholesky of the PSD Hankel part of ``kind`` on indices [j0, n).
 
     Returns (u [K][n], pivots) with u_r = l_r / sqrt(a_r) zero-extended below j0, so that
-    H[j0:, j0:] ~ sum_r u_r u_r^T.
+    H[j0:, j0:] ~ sum_r u_r u_r^T.  With ``weights`` w the factorisation (Fig. 2, same steps)
+    runs on W H W, entries w_j h_{j+k} w_k, and its factors are returned divided by w, so the
+    same identity holds; only the pivots (and the stop) differ.
     """
     t, h, d1, d2 = split(kind, params, n)
     j0 = first_index(kind, params)
     idx = np.arange(j0, n)
-    ells, a, piv = pivoted_cholesky(lambda p: h[idx + idx[p]], h[2 * idx], tol, kmax)
+    w = np.ones(len(idx)) if weights is None else np.asarray(weights, dtype=np.float64)[idx]
+    ells, a, piv = pivoted_cholesky(lambda p: h[idx + idx[p]] * w * w[p], h[2 * idx] * w * w,
+                                    tol, kmax)
     u = np.zeros((len(a), n))
     if len(a):
-        u[:, j0:] = ells / np.sqrt(a)[:, None]
+        u[:, j0:] = ells / np.sqrt(a)[:, None] / w
     return u, piv + j0
 
 
@@ -242,11 +256,14 @@ def truncation_bound(kind, params, n, u):
     return np.array(out)
 
 
-def target_rank(kind, params, n, target, tol=1e-18, kmax=128):
+def target_rank(kind, params, n, target, tol=1e-18, kmax=128, weighted=True):
     """Fewest rank terms K' whose ``truncation_bound`` is <= target, for the factors of a
-    pivoted Cholesky run to relative tolerance ``tol`` (at most kmax steps); all of them if
-    no prefix meets the target.  Returns (K', bound at K')."""
-    u, _ = hankel_factors(kind, params, n, tol, kmax)
+    pivoted Cholesky run to relative tolerance ``tol`` (at most kmax steps) on W H W
+    (``weighted``, w from ``pivot_weights``) or on H; all of them if no prefix meets the
+    target.  Returns (K', bound at K').  The bound is the same expression for weighted
+    factors: |D1_j / w_j| sqrt(w_j^2 d_j) = |D1_j| sqrt(d_j)."""
+    w = pivot_weights(kind, params, n) if weighted else None
+    u, _ = hankel_factors(kind, params, n, tol, kmax, weights=w)
     b = truncation_bound(kind, params, n, u)
     ok = np.nonzero(b <= target)[0]
     k = int(ok[0]) if len(ok) else len(u)

@@ -143,10 +143,27 @@ int build_step(Step& st, double tol, int target, int64_t kmax, int prec, cudaStr
         TDH_TRY(dev_alloc_t(&st.piv, (size_t)kcap));
         TDH_TRY(dev_alloc_t(&ubig, (size_t)kcap * n));
         int64_t K = 0;
-        int rc = pchol_run(st.h, n, st.j0, target ? kTargetRelTol : tol, kcap, ubig, st.piv, &K, s);
+        // accuracy-targeted plans pivot on the congruent W H W, w_j = sqrt(|D1_j D2_j|): the
+        // same A (D1 W^-1 (T o W H W) W^-1 D2), with the greedy step chasing the residual the
+        // output error weighs; the factors are converted back to factors of H (u_r / w)
+        double* w = nullptr;
+        int rc = TDH_OK;
+        if (target) {
+            rc = dev_alloc_t(&w, (size_t)n);
+            if (rc == TDH_OK)
+                rc = pchol_weights(st.d1, st.d2, st.scale_out, st.scale_in, n, w, s);
+        }
+        if (rc == TDH_OK)
+            rc = pchol_run(st.h, w, n, st.j0, target ? kTargetRelTol : tol, kcap, ubig, st.piv,
+                           &K, s);
         if (rc == TDH_OK && target && K > 0)
-            rc = pchol_truncate(st.h, ubig, n, st.j0, K, st.t, st.d1, st.d2, st.scale_out,
+            rc = pchol_truncate(st.h, w, ubig, n, st.j0, K, st.t, st.d1, st.d2, st.scale_out,
                                 st.scale_in, tol, &K, nullptr, s);
+        if (rc == TDH_OK && target && K > 0) rc = pchol_unweight(ubig, w, K, n, s);
+        if (w) {
+            cudaStreamSynchronize(s);
+            dev_free(w);
+        }
         if (rc == TDH_OK && K > 0) {
             rc = dev_alloc_t(&st.u64, (size_t)K * n);
             if (rc == TDH_OK) {

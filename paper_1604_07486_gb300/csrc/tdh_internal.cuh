@@ -54,19 +54,26 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
                    double* d2, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- a2
-// Pivoted Cholesky of H[j,k] = h[j+k], j,k in [j0,n); u: [kmax][n]; pivots: [kmax].
+// Pivoted Cholesky of H[j,k] = h[j+k] (w null) or of the congruent W H W, entries
+// w_j h[j+k] w_k (w: n positive weights), j,k in [j0,n); u: [kmax][n]; pivots: [kmax].
 // *K receives the rank (synchronises `s`).
-int pchol_run(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, double* u,
-              int64_t* pivots, int64_t* K, cudaStream_t s);
+int pchol_run(const double* h, const double* w, int64_t n, int64_t j0, double tol, int64_t kmax,
+              double* u, int64_t* pivots, int64_t* K, cudaStream_t s);
+// Weights w_j = sqrt(|D1_j D2_j|) of the accuracy-targeted factorisation (1 where zero), and
+// the conversion of factors of W H W back to factors of H (u[r][j] /= w_j).
+int pchol_weights(const double* d1, const double* d2, const double* so, const double* si,
+                  int64_t n, double* w, cudaStream_t s);
+int pchol_unweight(double* u, const double* w, int64_t K, int64_t n, cudaStream_t s);
 
-// Accuracy-targeted truncation of the rank-K factors u [K][n] of H (block j, k >= j0):
-// *Kout = the fewest terms K' <= K whose bound B(K') = max|t| max_j |D1_j| sqrt(d_j)
-// max_k |D2_k| sqrt(d_k) <= target (d: residual diagonal after K' steps; D1, D2 times the
-// optional scalings so, si), else K.  *bound (may be null) receives B(*Kout).  Synchronises s.
-int pchol_truncate(const double* h, const double* u, int64_t n, int64_t j0, int64_t K,
-                   const double* t, const double* d1, const double* d2, const double* so,
-                   const double* si, double target, int64_t* Kout, double* bound,
-                   cudaStream_t s);
+// Accuracy-targeted truncation of the rank-K factors u [K][n] of W H W (w null: of H; block
+// j, k >= j0): *Kout = the fewest terms K' <= K whose bound B(K') = max|t| max_j |D1_j / w_j|
+// sqrt(d_j) max_k |D2_k / w_k| sqrt(d_k) <= target (d: residual diagonal of W H W after K'
+// steps; D1, D2 times the optional scalings so, si), else K.  *bound (may be null) receives
+// B(*Kout).  Synchronises s.
+int pchol_truncate(const double* h, const double* w, const double* u, int64_t n, int64_t j0,
+                   int64_t K, const double* t, const double* d1, const double* d2,
+                   const double* so, const double* si, double target, int64_t* Kout,
+                   double* bound, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- a3-a7
 // FFT geometry of one execute configuration: L = C * LC points, local radix R.

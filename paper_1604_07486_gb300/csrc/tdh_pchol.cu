@@ -80,12 +80,13 @@ __device__ ArgMax block_argmax(ArgMax x) {
 
 // d_j = H_jj = h[2j] for j >= j0 (excluded indices get -inf); publish block argmax.
 __global__ void __launch_bounds__(kThreads) pchol_init(const double* __restrict__ h, int64_t n,
-                                                       int64_t j0, double* __restrict__ d,
+                                                       int64_t j0, const double* __restrict__ w,
+                                                       double* __restrict__ d,
                                                        ArgMax* __restrict__ part) {
     ArgMax best{-INFINITY, INT64_MAX};
     for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * kThreads) {
-        double v = (j >= j0) ? h[2 * j] : -INFINITY;
+        double v = (j >= j0) ? h[2 * j] * (w ? w[j] * w[j] : 1.0) : -INFINITY;
         d[j] = v;
         best = amax(best, ArgMax{v, j});
     }
@@ -94,8 +95,8 @@ __global__ void __launch_bounds__(kThreads) pchol_init(const double* __restrict_
 }
 
 __global__ void __launch_bounds__(kThreads) pchol_step(
-    const double* __restrict__ h, int64_t n, int64_t j0, double tol, int r,
-    double* __restrict__ u, int64_t* __restrict__ piv, double* __restrict__ d,
+    const double* __restrict__ h, int64_t n, int64_t j0, const double* __restrict__ w, double tol,
+    int r, double* __restrict__ u, int64_t* __restrict__ piv, double* __restrict__ d,
     const ArgMax* __restrict__ part_in, ArgMax* __restrict__ part_out, int nparts,
     State* __restrict__ st) {
     __shared__ double s_up[kKmaxShared];
@@ -117,8 +118,9 @@ __global__ void __launch_bounds__(kThreads) pchol_step(
     }
     for (int i = threadIdx.x; i < r; i += kThreads) s_up[i] = u[(int64_t)i * n + p];
     __syncthreads();
+    const double wp = w ? w[p] : 1.0;
     if (threadIdx.x == 0) {
-        double a = h[2 * p];
+        double a = h[2 * p] * wp * wp;
         for (int i = 0; i < r; ++i) a -= s_up[i] * s_up[i];
         s_a = a;
     }
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) pchol_step(
         double val = 0.0;
         double dj = -INFINITY;
         if (j >= j0) {
-            double c = h[j + p];
+            double c = h[j + p] * (w ? w[j] * wp : 1.0);
             for (int i = 0; i < r; ++i) c -= u[(int64_t)i * n + j] * s_up[i];
             val = c * inv;
             dj = d[j] - val * val;
@@ -158,8 +160,8 @@ __global__ void __launch_bounds__(kThreads) pchol_step(
 
 }  // namespace
 
-int pchol_run(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, double* u,
-              int64_t* pivots, int64_t* K, cudaStream_t s) {
+int pchol_run(const double* h, const double* w, int64_t n, int64_t j0, double tol, int64_t kmax,
+              double* u, int64_t* pivots, int64_t* K, cudaStream_t s) {
     if (kmax > kKmaxShared) kmax = kKmaxShared;
     if (kmax > n - j0) kmax = n - j0;
     int nblk = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 4 * (int64_t)sm_count());
@@ -175,11 +177,11 @@ int pchol_run(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, 
     {
         cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
         if (e == cudaSuccess) {
-            pchol_init<<<nblk, kThreads, 0, s>>>(h, n, j0, d, part);
+            pchol_init<<<nblk, kThreads, 0, s>>>(h, n, j0, w, d, part);
             e = cudaGetLastError();
         }
         for (int64_t r = 0; e == cudaSuccess && r < kmax; ++r) {
-            pchol_step<<<nblk, kThreads, 0, s>>>(h, n, j0, tol, (int)r, u, pivots, d,
+            pchol_step<<<nblk, kThreads, 0, s>>>(h, n, j0, w, tol, (int)r, u, pivots, d,
                                                  part + (r & 1) * nblk,
                                                  part + ((r + 1) & 1) * nblk, nblk, st);
             e = cudaGetLastError();
@@ -231,7 +233,7 @@ __device__ __forceinline__ double warp_max(double v) {
 __global__ void __launch_bounds__(kThreads) k_trunc_bound(
     const double* __restrict__ h, const double* __restrict__ u, int64_t n, int64_t j0, int K,
     const double* __restrict__ t, const double* __restrict__ d1, const double* __restrict__ d2,
-    const double* __restrict__ so, const double* __restrict__ si,
+    const double* __restrict__ so, const double* __restrict__ si, const double* __restrict__ w,
     unsigned long long* __restrict__ m) {
     const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const bool in = j < n;
@@ -239,9 +241,10 @@ __global__ void __launch_bounds__(kThreads) k_trunc_bound(
     const int lane = threadIdx.x & 31;
     const double tm = warp_max(in ? fabs(t[j]) : 0.0);
     if (lane == 0) atomic_max_nonneg(&m[0], tm);
-    const double a1 = blk ? fabs(d1[j] * (so ? so[j] : 1.0)) : 0.0;
-    const double a2 = blk ? fabs(d2[j] * (si ? si[j] : 1.0)) : 0.0;
-    double dj = blk ? h[2 * j] : 0.0;
+    const double wj = (blk && w) ? w[j] : 1.0;
+    const double a1 = blk ? fabs(d1[j] * (so ? so[j] : 1.0)) / wj : 0.0;
+    const double a2 = blk ? fabs(d2[j] * (si ? si[j] : 1.0)) / wj : 0.0;
+    double dj = blk ? h[2 * j] * wj * wj : 0.0;
     for (int k = 0; k <= K; ++k) {
         const double sq = sqrt(fmax(dj, 0.0));
         const double v1 = warp_max(a1 * sq), v2 = warp_max(a2 * sq);
@@ -256,12 +259,44 @@ __global__ void __launch_bounds__(kThreads) k_trunc_bound(
     }
 }
 
+// w_j = sqrt(|D1_j D2_j|) (with the step's scalings), 1 where that is 0 or not finite.
+__global__ void k_pivot_weights(const double* __restrict__ d1, const double* __restrict__ d2,
+                                const double* __restrict__ so, const double* __restrict__ si,
+                                int64_t n, double* __restrict__ w) {
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (j >= n) return;
+    const double v = sqrt(fabs(d1[j] * (so ? so[j] : 1.0) * d2[j] * (si ? si[j] : 1.0)));
+    w[j] = (v > 0.0 && isfinite(v)) ? v : 1.0;
+}
+
+// u[r][j] /= w_j: factors of W H W -> factors of H
+__global__ void k_unweight(double* __restrict__ u, const double* __restrict__ w, int64_t K,
+                           int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < K * n) u[i] /= w[i % n];
+}
+
 }  // namespace
 
-int pchol_truncate(const double* h, const double* u, int64_t n, int64_t j0, int64_t K,
-                   const double* t, const double* d1, const double* d2, const double* so,
-                   const double* si, double target, int64_t* Kout, double* bound,
-                   cudaStream_t s) {
+int pchol_weights(const double* d1, const double* d2, const double* so, const double* si,
+                  int64_t n, double* w, cudaStream_t s) {
+    k_pivot_weights<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(d1, d2, so, si,
+                                                                                  n, w);
+    TDH_CUDA(cudaGetLastError());
+    return TDH_OK;
+}
+
+int pchol_unweight(double* u, const double* w, int64_t K, int64_t n, cudaStream_t s) {
+    if (K <= 0) return TDH_OK;
+    k_unweight<<<(unsigned)((K * n + kThreads - 1) / kThreads), kThreads, 0, s>>>(u, w, K, n);
+    TDH_CUDA(cudaGetLastError());
+    return TDH_OK;
+}
+
+int pchol_truncate(const double* h, const double* w, const double* u, int64_t n, int64_t j0,
+                   int64_t K, const double* t, const double* d1, const double* d2,
+                   const double* so, const double* si, double target, int64_t* Kout,
+                   double* bound, cudaStream_t s) {
     *Kout = K;
     if (K <= 0) return TDH_OK;
     const size_t words = 2 * (size_t)K + 3;
@@ -271,7 +306,7 @@ int pchol_truncate(const double* h, const double* u, int64_t n, int64_t j0, int6
     cudaError_t e = cudaMemsetAsync(m, 0, sizeof(unsigned long long) * words, s);
     if (e == cudaSuccess) {
         const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-        k_trunc_bound<<<blocks, kThreads, 0, s>>>(h, u, n, j0, (int)K, t, d1, d2, so, si, m);
+        k_trunc_bound<<<blocks, kThreads, 0, s>>>(h, u, n, j0, (int)K, t, d1, d2, so, si, w, m);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -310,7 +345,7 @@ extern "C" int tdh_pchol(const double* h, int64_t n, int64_t j0, double tol, int
         tdh::set_error("tdh_pchol: need n >= 1, j0 in {0,1} < n, tol > 0, kmax >= 1, non-NULL");
         return TDH_ERR_INVALID_ARG;
     }
-    return tdh::pchol_run(h, n, j0, tol, kmax, u, pivots, K, tdh::as_stream(stream));
+    return tdh::pchol_run(h, nullptr, n, j0, tol, kmax, u, pivots, K, tdh::as_stream(stream));
 }
 
 // ----------------------------------------------------------------------------------------
@@ -395,11 +430,11 @@ extern "C" int tdh_pchol_noalloc(const double* h, int64_t n, int64_t j0, double 
     State host{0.0, 0, 0};
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
     if (e == cudaSuccess) {
-        pchol_init<<<nblk, kThreads, 0, s>>>(h, n, j0, d, part);
+        pchol_init<<<nblk, kThreads, 0, s>>>(h, n, j0, nullptr, d, part);
         e = cudaGetLastError();
     }
     for (int64_t r = 0; e == cudaSuccess && r < kmax; ++r) {
-        pchol_step<<<nblk, kThreads, 0, s>>>(h, n, j0, tol, (int)r, u, pivots, d,
+        pchol_step<<<nblk, kThreads, 0, s>>>(h, n, j0, nullptr, tol, (int)r, u, pivots, d,
                                              part + (r & 1) * nblk, part + ((r + 1) & 1) * nblk,
                                              nblk, st);
         e = cudaGetLastError();

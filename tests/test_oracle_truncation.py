@@ -60,11 +60,14 @@ def _mutated_bound(kind, params, n, u, mutation):
     return np.array(out)
 
 
+@pytest.mark.parametrize("weighted", [False, True])
 @pytest.mark.parametrize("kind,params", KINDS)
-def test_bound_dominates_dense_error(kind, params):
-    """Every prefix: max |A - A_K'| <= B(K') (up to the rounding of the dense product)."""
+def test_bound_dominates_dense_error(kind, params, weighted):
+    """Every prefix: max |A - A_K'| <= B(K') (up to the rounding of the dense product), for
+    the factors of H and for those of the congruent W H W (pivot weights), converted back."""
     n = 56
-    u, _ = oracle.hankel_factors(kind, params, n, 1e-18, kmax=n)
+    w = oracle.pivot_weights(kind, params, n) if weighted else None
+    u, _ = oracle.hankel_factors(kind, params, n, 1e-18, kmax=n, weights=w)
     b = oracle.truncation_bound(kind, params, n, u)
     errs, scale = _dense_errors(kind, params, n, u)
     assert len(b) == len(u) + 1 and len(u) >= 8
@@ -104,7 +107,8 @@ def test_target_rank_meets_target(kind, params):
     j = np.arange(n)
     T = np.where(j[None, :] >= j[:, None], t[np.abs(j[None, :] - j[:, None])], 0.0)
     A = oracle.entries(kind, params, n)
-    u, _ = oracle.hankel_factors(kind, params, n, 1e-18, kmax=128)
+    u, _ = oracle.hankel_factors(kind, params, n, 1e-18, kmax=128,
+                                 weights=oracle.pivot_weights(kind, params, n))
     for target in (1e-3, 1e-6, 1e-9, 1e-12):
         k, bound = oracle.target_rank(kind, params, n, target)
         assert k >= prev and bound <= target
@@ -114,3 +118,20 @@ def test_target_rank_meets_target(kind, params):
         Ak[:, :j0] = A[:, :j0]
         err = np.abs(alpha @ (A - Ak).T).max(axis=1) / np.abs(alpha).sum(axis=1)
         assert err.max() <= target, (target, k, err.max())
+
+
+def test_weighted_pivots_need_fewer_terms_for_chebyshev_to_legendre():
+    """Chebyshev -> Legendre has D1 and D2 growing like j: pivoting on W H W (w = sqrt|D1 D2|)
+    reaches a worst-case target with fewer terms than pivoting on H, and the weighted
+    factors reproduce H as well as the unweighted ones at full rank."""
+    n = 4096
+    for target in (2.5e-6, 1e-8):
+        kw, _ = oracle.target_rank(oracle.CHEB2LEG, None, n, target, weighted=True)
+        ku, _ = oracle.target_rank(oracle.CHEB2LEG, None, n, target, weighted=False)
+        assert kw < ku, (target, kw, ku)
+    n = 300
+    _, h, _, _ = oracle.split(oracle.CHEB2LEG, None, n)
+    H = oracle.hankel(h, n, 1)
+    u, _ = oracle.hankel_factors(oracle.CHEB2LEG, None, n, 1e-18, kmax=n,
+                                 weights=oracle.pivot_weights(oracle.CHEB2LEG, None, n))
+    assert np.abs(H - u[:, 1:].T @ u[:, 1:]).max() <= 1e-13 * np.abs(H).max()
