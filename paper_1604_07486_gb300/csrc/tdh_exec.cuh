@@ -668,10 +668,9 @@ int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
     constexpr size_t smem = (size_t)(padded_len<V>(G.LC()) + G.LC() / 2 + G.twp_len()) * sizeof(V);
     static_assert(smem <= 232448, "shared memory budget");
     auto kern = exec_kernel<T, LOGLC, R, C, NT, MINB, RAGGED>;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static PerDevice attr_once;
+    const cudaError_t attr_err = per_device(attr_once, [&](int*) {
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (attr_err != cudaSuccess) {
         set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(attr_err));
@@ -691,19 +690,16 @@ int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    // persistent: as many clusters as can be resident (queried once per kernel)
-    static std::once_flag once_res;
-    static int resident = 0;
-    static cudaError_t res_err = cudaSuccess;
-    std::call_once(once_res, [&] {
-        if (C > 1) {
-            res_err = cudaOccupancyMaxActiveClusters(&resident, kern, &cfg);
-        } else {
-            int per_sm = 0;
-            res_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
-            resident = per_sm * sm_count();
-        }
-    });
+    // persistent: as many clusters as can be resident (queried once per kernel and device)
+    static PerDevice res_once;
+    int resident = 0;
+    const cudaError_t res_err = per_device(res_once, [&](int* out) {
+        if (C > 1) return cudaOccupancyMaxActiveClusters(out, kern, &cfg);
+        int per_sm = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+        *out = per_sm * sm_count();
+        return e;
+    }, &resident);
     if (res_err != cudaSuccess) {
         set_error("occupancy query: %s", cudaGetErrorString(res_err));
         return TDH_ERR_CUDA;

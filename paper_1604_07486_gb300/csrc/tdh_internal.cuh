@@ -45,6 +45,26 @@ void scratch_free(void* p, cudaStream_t s);
 
 int sm_count();
 
+// One-time set-up per device (kernel attributes, occupancy queries): `f(int* val)` returns a
+// cudaError_t and runs once for each device that is current when it is needed; its result
+// code and *val are kept per device.
+constexpr int kDeviceSlots = 64;
+struct PerDevice {
+    std::once_flag flag[kDeviceSlots];
+    cudaError_t err[kDeviceSlots] = {};
+    int val[kDeviceSlots] = {};
+};
+template <typename F>
+cudaError_t per_device(PerDevice& pd, F&& f, int* val = nullptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kDeviceSlots) return cudaErrorInvalidDevice;
+    std::call_once(pd.flag[dev], [&] { pd.err[dev] = f(&pd.val[dev]); });
+    if (val) *val = pd.val[dev];
+    return pd.err[dev];
+}
+
 // Count kernel launches made by execute calls (reported by tdh_launch_count).
 void note_launches(int64_t k);
 

@@ -461,11 +461,10 @@ int cross16_launch(const MPParams<T>& Q, int64_t nb, cudaStream_t s) {
     using V = typename cx<T>::t;
     constexpr int PP = 4096 / C;
     constexpr size_t smem = (size_t)((sizeof(T) == 8 ? 2 : 1) * PP * (C + 1) + C) * sizeof(V);
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [&] {
-        err = cudaFuncSetAttribute(mp_cross16<T, LC, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem);
+    static PerDevice attr_once;
+    const cudaError_t err = per_device(attr_once, [&](int*) {
+        return cudaFuncSetAttribute(mp_cross16<T, LC, C>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
     if (err != cudaSuccess) {
         set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(err));
@@ -573,19 +572,18 @@ int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjo
 
     constexpr size_t smem_pass = (size_t)(padded_len<V>(LC) + G.twp_len()) * sizeof(V);
     const size_t smem_cross = (size_t)(16 * (P.C + 1) + P.C / 2) * sizeof(V);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(mp_fwd<T, LOGLC, R, NT>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pass);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(mp_inv<T, LOGLC, R, NT>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem_pass);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(mp_cross<T, LC>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(sizeof(V) * (16 * 513 + 256)));
+    static PerDevice attr_once;
+    const cudaError_t attr_err = per_device(attr_once, [&](int*) {
+        cudaError_t e = cudaFuncSetAttribute(mp_fwd<T, LOGLC, R, NT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_pass);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mp_inv<T, LOGLC, R, NT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_pass);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(mp_cross<T, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(V) * (16 * 513 + 256)));
+        return e;
     });
     int rc = TDH_OK;
     if (attr_err != cudaSuccess) {

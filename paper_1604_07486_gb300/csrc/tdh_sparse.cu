@@ -571,14 +571,15 @@ int inverse_typed(const Step& st, const void* in, void* out, int64_t batch, int 
     }
     using A = Aff<T, OFF>;
     constexpr size_t smem = 3 * sizeof(T) * (size_t)Scan<T>::smem;
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
+    static PerDevice attr_once;
+    const cudaError_t attr = per_device(attr_once, [](int*) {
         const void* ks[4] = {(const void*)k_scan_tiles<T, OFF, 0>, (const void*)k_scan_tiles<T, OFF, 1>,
                              (const void*)k_scan_solve<T, OFF, 0>, (const void*)k_scan_solve<T, OFF, 1>};
+        cudaError_t e = cudaSuccess;
         for (const void* k : ks)
-            if (attr == cudaSuccess)
-                attr = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return e;
     });
     if (attr != cudaSuccess) {
         set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(attr));
