@@ -691,7 +691,11 @@ int time_config(const ConfigRef& r, int64_t batch, const TuneBuffers& tb, cudaSt
 template <typename T>
 int autotune_typed(tdh_plan_s& plan, int64_t batch, cudaStream_t s) {
     const int prec = plan.params.prec;
-    std::vector<ConfigRef> cfgs = plan_configs(plan);
+    std::vector<ConfigRef> cfgs;
+    for (const ConfigRef& r : plan_configs(plan))  // only what has a choice to make
+        if (schedule_candidates(prec, config_data(r).g.logL, r.cls >= 0).size() > 1)
+            cfgs.push_back(r);
+    if (cfgs.empty()) return TDH_OK;
     int64_t elems = 0, bmax = 0;
     for (const ConfigRef& r : cfgs) {
         int64_t b, len;
@@ -725,6 +729,11 @@ int autotune_typed(tdh_plan_s& plan, int64_t batch, cudaStream_t s) {
             return TDH_ERR_CUDA;
         }
     k_fill_test<T><<<blocks_for(elems), kThreads, 0, s>>>(static_cast<T*>(tb.in), elems);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_error("autotune: input fill launch failed");
+        cleanup();
+        return TDH_ERR_CUDA;
+    }
     for (const ConfigRef& r : cfgs) {
         const std::vector<Geometry> cands =
             schedule_candidates(prec, config_data(r).g.logL, r.cls >= 0);

@@ -158,3 +158,18 @@ def test_schedule_errors(tdh):
     import ctypes
     info = (ctypes.c_int * 8)()
     assert tdh.lib().tdh_plan_schedule_info(plan._h, 1, info) == -1
+
+
+def test_plans_without_fft_steps(tdh):
+    """A conversion made only of banded factors (ultraspherical 0.25 -> 1.25, Case 1) has no
+    execute configuration: the schedule calls have nothing to do and succeed."""
+    import torch
+    n = 4096
+    plan = tdh.Plan("ultra2ultra", n, prec="fp32", tol=1e-13, params=(0.25, 1.25))
+    assert plan.schedules() == []
+    plan.set_schedule(3)
+    assert plan.autotune(4) == []
+    alpha = workloads.coefficients(n, 2, decay=1.0, seed=14)
+    ref = oracle.matvec(oracle.ULTRA, (0.25, 1.25), alpha)
+    y = plan.execute(torch.tensor(alpha, dtype=torch.float32, device="cuda"))
+    assert _err(y.double().cpu().numpy(), ref, alpha, None) <= TOL["fp32"]
