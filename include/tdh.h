@@ -207,6 +207,14 @@ int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max);
  * captured from the plan before the change must not be replayed after it.
  */
 int tdh_plan_schedule_count(tdh_plan_t plan, int* count);
+/*
+ * tdh_schedules -- host only (no device call): the compiled schedules for an FFT of 2^logL
+ * points in precision prec, the default first (ragged != 0: only those usable by ragged
+ * batches, i.e. within one cluster).  out (host, 6 ints per schedule: log2 LC, C, R, NT,
+ * MINB, 1 if multi-pass) receives at most cap schedules; *count the number there are (0 when
+ * no kernel covers that length).  Errors: INVALID_ARG.
+ */
+int tdh_schedules(int prec, int logL, int ragged, int* out, int cap, int* count);
 int tdh_plan_schedule_info(tdh_plan_t plan, int config, int* info);
 int tdh_plan_set_schedule(tdh_plan_t plan, int index, void* stream);
 int tdh_plan_autotune(tdh_plan_t plan, int64_t batch, void* stream);

@@ -24,7 +24,7 @@ EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "t
            "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol", "tdh_pchol_noalloc",
            "tdh_plan_execute_ragged", "tdh_launch_count", "tdh_plan_execute_host",
            "tdh_plan_schedule_count", "tdh_plan_schedule_info", "tdh_plan_set_schedule",
-           "tdh_plan_autotune")
+           "tdh_plan_autotune", "tdh_schedules")
 FLAG_RAGGED = 1
 FLAG_TARGET = 2
 
@@ -75,6 +75,9 @@ def lib():
         L.tdh_plan_schedule_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.tdh_plan_set_schedule.argtypes = [vp, ctypes.c_int, vp]
         L.tdh_plan_autotune.argtypes = [vp, i64, vp]
+        L.tdh_schedules.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int)]
         for name in EXPORTS:
             if name != "tdh_last_error":
                 getattr(L, name).restype = ctypes.c_int
@@ -240,6 +243,18 @@ def pchol(h, n, j0, tol, kmax=128, stream=None):
                            ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(piv.data_ptr()),
                            ctypes.byref(K), _stream(stream)))
     return u[: K.value].clone(), piv[: K.value].clone()
+
+
+def compiled_schedules(prec, logL, ragged=False):
+    """The compiled execute schedules for an FFT of 2^logL points (tdh_schedules, no device
+    needed): dicts with log2 LC, C, R, NT, MINB and the multi-pass flag, default first."""
+    prec = PRECS[prec] if isinstance(prec, str) else int(prec)
+    n = ctypes.c_int()
+    _check(lib().tdh_schedules(prec, int(logL), int(bool(ragged)), None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_int * (6 * max(n.value, 1)))()
+    _check(lib().tdh_schedules(prec, int(logL), int(bool(ragged)), buf, n.value, ctypes.byref(n)))
+    keys = ("logLC", "C", "R", "NT", "MINB", "multipass")
+    return [dict(zip(keys, list(buf[6 * i:6 * i + 6]))) for i in range(n.value)]
 
 
 def launch_count():

@@ -687,6 +687,16 @@ int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max) {
     return TDH_OK;
 }
 
+int tdh_schedules(int prec, int logL, int ragged, int* out, int cap, int* count) {
+    clear_error();
+    if ((prec != TDH_FP32 && prec != TDH_FP64) || logL < 1 || logL > 62 || cap < 0 || !count ||
+        (cap > 0 && !out)) {
+        set_error("tdh_schedules: need a known precision, 1 <= logL <= 62, cap >= 0, non-NULL");
+        return TDH_ERR_INVALID_ARG;
+    }
+    return exec_schedules(prec, logL, ragged, out, cap, count);
+}
+
 int tdh_plan_schedule_count(tdh_plan_t plan, int* count) {
     clear_error();
     if (!plan || !count) {

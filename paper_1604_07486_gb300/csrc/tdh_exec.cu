@@ -758,6 +758,16 @@ int autotune_typed(tdh_plan_s& plan, int64_t batch, cudaStream_t s) {
 
 }  // namespace
 
+int exec_schedules(int prec, int logL, int ragged, int* out, int cap, int* count) {
+    const std::vector<Geometry> c = schedule_candidates(prec, logL, ragged != 0);
+    *count = (int)c.size();
+    for (int i = 0; i < (int)c.size() && i < cap; ++i) {
+        const int v[6] = {c[i].logLC, c[i].C, c[i].R, c[i].NT, c[i].MINB, c[i].C > 8 ? 1 : 0};
+        for (int k = 0; k < 6; ++k) out[6 * i + k] = v[k];
+    }
+    return TDH_OK;
+}
+
 int exec_schedule_count(const tdh_plan_s& plan) {
     return (int)plan_configs(const_cast<tdh_plan_s&>(plan)).size();
 }

@@ -210,6 +210,7 @@ int exec_launch_ragged(const Step& st, int prec, const void* in, void* out, cons
 // Execute schedules (FFT geometries with a compiled kernel) of the plan's T o H steps.
 // Configurations in order: each T o H step's dense configuration, then (ragged plans) one per
 // FFT length class.  info = {log2 L, log2 LC, C, R, NT, MINB, index, count}.
+int exec_schedules(int prec, int logL, int ragged, int* out, int cap, int* count);
 int exec_schedule_count(const tdh_plan_s& plan);
 int exec_schedule_info(const tdh_plan_s& plan, int config, int* info);
 // Every configuration takes its schedule min(index, count - 1) (tables rebuilt as needed).

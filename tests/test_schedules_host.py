@@ -1,0 +1,92 @@
+"""The execute-schedule enumeration (host logic, no GPU needed): for every FFT length the
+library can convert, the default schedule comes first and every schedule is a valid split of
+the transform that the kernels' static shape rules accept."""
+import pytest
+
+FP64, FP32 = 0, 1
+SMEM_MAX = 232448  # bytes of dynamic shared memory a CTA may opt into
+
+
+@pytest.fixture(scope="module")
+def tdh():
+    from paper_1604_07486_gb300 import build
+    import paper_1604_07486_gb300 as m
+    build.build()
+    return m
+
+
+def _radix(prec, logLC):
+    return 16 if prec == FP32 and logLC > 9 else 8
+
+
+def _passes(logLC, R):
+    """Radices of the local passes: radix-R passes and a trailing smaller radix."""
+    logR = R.bit_length() - 1
+    npr = logLC // logR
+    rest = 1 << (logLC - npr * logR)
+    return [R] * npr + ([rest] if rest > 1 else [])
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_default_schedule_rule(tdh, prec):
+    """Default: the largest local FFT shared memory holds (2^14 float32, 2^13 float64), the
+    fewest CTAs per vector; half-size slices for multi-pass FFTs of up to 128 full slices."""
+    cap = 14 if prec == FP32 else 13
+    for logL in range(8, cap + 10):  # up to 512 slices
+        sched = tdh.compiled_schedules(prec, logL)
+        d = sched[0]
+        if logL <= cap:
+            assert (d["logLC"], d["C"]) == (logL, 1), (logL, d)
+        elif (1 << (logL - cap)) <= 8:
+            assert (d["logLC"], d["C"]) == (cap, 1 << (logL - cap)), (logL, d)
+        elif (1 << (logL - cap)) <= 128:
+            assert (d["logLC"], d["C"], d["multipass"]) == (cap - 1, 1 << (logL - cap + 1), 1)
+        else:
+            assert (d["logLC"], d["C"], d["multipass"]) == (cap, 1 << (logL - cap), 1)
+        assert d["MINB"] == (2 if d["multipass"] and d["logLC"] == cap - 1 else 1)
+
+
+@pytest.mark.parametrize("ragged", [False, True])
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_every_schedule_is_a_valid_split(tdh, prec, ragged):
+    seen_any = 0
+    for logL in range(8, (14 if prec == FP32 else 13) + 10):
+        sched = tdh.compiled_schedules(prec, logL, ragged)
+        keys = [(s["logLC"], s["C"], s["NT"], s["MINB"]) for s in sched]
+        assert len(set(keys)) == len(keys), (logL, keys)
+        for s in sched:
+            seen_any += 1
+            lc, C, R, NT = s["logLC"], s["C"], s["R"], s["NT"]
+            assert lc + C.bit_length() - 1 == logL, (logL, s)
+            assert R == _radix(prec, lc)
+            assert s["multipass"] == (1 if C > 8 else 0)
+            if ragged:
+                assert C <= 8
+            if C > 8:
+                assert 16 <= C <= 512
+                continue
+            LC, es = 1 << lc, (8 if prec == FP32 else 16)
+            S0 = LC // R
+            assert S0 % NT == 0 and S0 // NT >= 1, s  # pass-0 groups divide over threads
+            assert len(_passes(lc, R)) >= 2
+            if C > 1:
+                assert (LC // C) % (2 * NT) == 0, s  # cross stage: two positions per thread
+            assert NT * s["MINB"] <= 2048 and 65536 // (NT * s["MINB"]) >= 32
+            assert LC * es + (LC // 2) * es <= SMEM_MAX  # FFT buffer and scaled input
+    assert seen_any > 30
+
+
+def test_lengths_without_a_kernel(tdh):
+    """Beyond 512 slices nothing is compiled; ragged batches stop at one cluster."""
+    assert tdh.compiled_schedules(FP32, 24) == []
+    assert tdh.compiled_schedules(FP64, 23) == []
+    assert tdh.compiled_schedules(FP32, 18, ragged=True) == []
+    assert tdh.compiled_schedules(FP32, 17, ragged=True)[0]["C"] == 8
+
+
+def test_bad_arguments(tdh):
+    import ctypes
+    n = ctypes.c_int()
+    assert tdh.lib().tdh_schedules(7, 10, 0, None, 0, ctypes.byref(n)) == -1
+    assert tdh.lib().tdh_schedules(FP32, 0, 0, None, 0, ctypes.byref(n)) == -1
+    assert tdh.lib().tdh_schedules(FP32, 10, 0, None, 3, ctypes.byref(n)) == -1
