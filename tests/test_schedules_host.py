@@ -73,7 +73,7 @@ def test_every_schedule_is_a_valid_split(tdh, prec, ragged):
                 assert (LC // C) % (2 * NT) == 0, s  # cross stage: two positions per thread
             assert NT * s["MINB"] <= 2048 and 65536 // (NT * s["MINB"]) >= 32
             assert LC * es + (LC // 2) * es <= SMEM_MAX  # FFT buffer and scaled input
-    assert seen_any > 30
+    assert seen_any > 20
 
 
 def test_lengths_without_a_kernel(tdh):
