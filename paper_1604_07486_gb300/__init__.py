@@ -110,14 +110,19 @@ class Plan:
     """A conversion plan (tdh_plan_create): symbols, pivoted Cholesky and FFT tables for
     vectors of n coefficients, built on the current CUDA device in float64.  tol is relative
     to max diag(H); with target=True it is the accuracy asked of the truncation instead
-    (fewest rank terms whose residual bound gives max|beta_K - beta| <= tol ||alpha||_1)."""
+    (fewest rank terms whose residual bound gives max|beta_K - beta| <= tol ||alpha||_1).
+    Without tol the plan is accuracy-targeted at 2.5e-6 (float32) or 5e-13 (float64)."""
 
     def __init__(self, kind, n, prec="fp32", tol=None, params=(), kmax=0, ragged=False,
-                 target=False):
+                 target=None):
         self.kind = _kind(kind)
         self.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
         if tol is None:
-            tol = 1e-15 if self.prec == FP64 else 1e-7
+            # default: accuracy-targeted at half the precision's tolerance (5e-6 float32,
+            # 1e-12 float64, of ||alpha||_1), guaranteed for every input
+            tol = 5e-13 if self.prec == FP64 else 2.5e-6
+            target = True if target is None else target
+        target = bool(target)
         p = _Params()
         for i, v in enumerate(params):
             p.p[i] = float(v)
