@@ -22,6 +22,10 @@ matrices" (arXiv:1604.07486).
   end): a Jacobi (-1/2, -1/2) conversion and a diagonal scaling.
 * ``fast_matvec`` is the outline of Fig. 1 in float64 with numpy's FFT as the Toeplitz
   step; it is a CPU timing reference only, never the parity truth.
+* ``truncation_bound`` / ``target_rank`` / ``pivot_weights``: the accuracy-targeted choice of
+  the rank (a reading, not in the paper): the PSD residual of the Fig. 2 factorisation bounds
+  every entry of A - A_K; the factorisation may pivot on W H W (w = sqrt|d1 d2|), the same A.
+  Pinned against dense residuals by brute force (tests/test_oracle_truncation.py).
 """
 import ctypes
 import os
