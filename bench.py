@@ -145,6 +145,17 @@ def measured_peaks():
         return {}
 
 
+def arith_peaks(tdh):
+    """FP32 (FFMA) and FP64 (DFMA) throughput measured on this device by the library's probe
+    (tdh_measure_fma_rate: best of three launches of independent FMA chains on every SM), in
+    TFLOP/s, with the SM count read from the device."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return {"fp32": tdh.measure_fma_rate("fp32"), "fp64": tdh.measure_fma_rate("fp64"),
+            "sms": props.multi_processor_count,
+            "note": "measured: FMA-chain probe on every SM (tdh_measure_fma_rate), 2 flop per FMA"}
+
+
 def profile_traffic():
     """dram bytes per launch from the committed ncu summary, if it matches this kernel."""
     try:
@@ -223,35 +234,20 @@ def cpu_model():
 
 
 def cpu_fast_sample():
-    """The same algorithm (Fig. 1) on the host for comparison: float64, split and Fig. 2
-    Cholesky from the oracle (plan, not timed), then v = D2 alpha, w = sum_r u_r o
-    T(u_r o v) with every Toeplitz product by scipy.fft on all host cores, beta = D1 w (+ row 0
-    for Chebyshev-to-Legendre), 16 vectors of n = 65536, both directions."""
-    import numpy as np
-    import scipy.fft as sf
+    """The same algorithm (Fig. 1) on the host for comparison: oracle.fast_plan builds the
+    float64 plan (split and Fig. 2 factors, not timed), oracle.fast_apply runs v = D2 alpha,
+    w = sum_r u_r o T(u_r o v) with every Toeplitz product by scipy.fft on all host cores,
+    beta = D1 w (+ row 0 for Chebyshev-to-Legendre); 16 vectors of n = 65536, both
+    directions."""
     import oracle
     import workloads
     B, workers = 16, os.cpu_count() or 1
     alpha = workloads.coefficients(N, B, decay=DECAY, seed=0)
-    L = 1
-    while L < 2 * N - 1:
-        L *= 2
     seconds = 0.0
     for kind, tol in ((oracle.LEG2CHEB, TOL64["leg2cheb"]), (oracle.CHEB2LEG, TOL64["cheb2leg"])):
-        t, h, d1, d2 = oracle.split(kind, None, N)
-        u, _ = oracle.hankel_factors(kind, None, N, tol)
-        spec = np.conj(sf.rfft(t, L))
-        row0 = oracle.entries(kind, None, N, 0, 1)[0] if kind == oracle.CHEB2LEG else None
+        plan = oracle.fast_plan(kind, None, N, tol)
         t0 = time.perf_counter()
-        v = alpha * d2
-        w = np.zeros_like(v)
-        for ur in u:
-            y = sf.irfft(sf.rfft(v * ur, L, axis=-1, workers=workers) * spec, L, axis=-1,
-                         workers=workers)[:, :N]
-            w += ur * y
-        beta = w * d1
-        if row0 is not None:
-            beta[:, 0] = alpha @ row0
+        oracle.fast_apply(plan, alpha, workers=workers)
         seconds += time.perf_counter() - t0
     return {"value": 2 * N * B / seconds, "unit": "coeffs/s", "cores": workers,
             "kind": "same algorithm on the host: float64, scipy.fft (pocketfft) on all cores",
@@ -273,6 +269,48 @@ def cpu_baseline_sample():
             "seconds": dt, "cpu_model": cpu_model()}
 
 
+def precision_comparison(tdh, args, flush, stream, world, rank, n=1 << 20, batch=16):
+    """Legendre -> Chebyshev at n coefficients, float32 and float64 execute on the same
+    vectors (accuracy-targeted plans, each tuned), CUDA events on the launch stream, L2
+    flushed before every timed repetition; errors against the oracle on sampled rows."""
+    import numpy as np
+    import torch
+    alpha = workloads_coefficients(n, batch, rank)
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.r_[np.arange(16), n - 1 - np.arange(16), rng.integers(0, n, 32)])
+    out = {"workload": f"leg2cheb n={n} batch={batch}", "n": n, "batch": batch}
+    for prec, plan_kw, reps in (("fp32", PLAN32["leg2cheb"], 10), ("fp64", PLAN64["leg2cheb"], 5)):
+        plan = tdh.Plan("leg2cheb", n, prec=prec, **plan_kw)
+        _, sched = tune(plan, batch, args)
+        x = torch.tensor(alpha, dtype=plan.dtype, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(2):
+            plan.execute(x, out=y)
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(reps):
+            flush.fill_(i)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.execute(x, out=y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        err = oracle_error(alpha, y.double().cpu().numpy(), "leg2cheb", [0, batch - 1], rows) \
+            if rank == 0 else None
+        out[prec] = {"value": world * n * batch / (statistics.median(ms) / 1e3), "unit": "coeffs/s",
+                     "ms_median": statistics.median(ms), "reps": reps, "K": plan.K, "plan": plan_kw,
+                     "schedule": sched, "error_vs_oracle": err}
+        plan.close()
+    out["speedup_fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def workloads_coefficients(n, batch, seed):
+    import workloads
+    return workloads.coefficients(n, batch, decay=DECAY, seed=seed)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -281,6 +319,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-big", action="store_true",
+                    help="skip the float32-vs-float64 comparison at n = 2^20")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep every plan on its default execute schedule")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
@@ -371,8 +411,8 @@ def main():
     achieved = flops / (total_ms / 1e3) / 1e12
     clocks = sampler.summary()
     peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FFMA lanes x 2 flop x max SM clock
+    apeaks = arith_peaks(tdh)
+    fp32_peak = apeaks["fp32"]
     hbm = peaks.get("hbm_gbs", 6649.7)
     hbm_achieved = 8.0 * coeffs_per_step * args.steps / (total_ms / 1e3) / 1e9
 
@@ -394,7 +434,7 @@ def main():
         step(plans64, x64, y64)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 2
+        reps = 5
         ms64 = 0.0
         for i in range(reps):
             flush.fill_(i)
@@ -407,10 +447,21 @@ def main():
         if rank == 0:
             for k in KINDS:
                 err64[k] = oracle_error(alpha, y64[k].cpu().numpy(), k, [0, BATCH - 1], rows)
+        flops64 = sum(flops_per_vector(plans64[k].K, L) * BATCH for k in KINDS)
         fp64 = {"value": world * coeffs_per_step * reps / (ms64 / 1e3), "unit": "coeffs/s",
-                "ms_per_step": ms64 / reps, "K": {k: plans64[k].K for k in KINDS},
-                "plans": PLAN64, "error_vs_oracle": err64, "schedule": tuned64}
+                "ms_per_step": ms64 / reps, "reps": reps, "K": {k: plans64[k].K for k in KINDS},
+                "plans": PLAN64, "error_vs_oracle": err64, "schedule": tuned64,
+                "roofline": {"bound": "alu", "achieved": flops64 / (ms64 / reps / 1e3) / 1e12,
+                             "peak": apeaks["fp64"], "unit": "TFLOP/s",
+                             "frac": flops64 / (ms64 / reps / 1e3) / 1e12 / apeaks["fp64"],
+                             "peak_note": "FP64 DFMA " + apeaks["note"]}}
         del plans64, x64, y64
+
+    # the benchmark spec's precision claim across n = 2^16 .. 2^20: float32 against float64 at
+    # n = 2^20 (multi-pass FFTs), Legendre -> Chebyshev, batch 16
+    big = None
+    if not args.no_fp64 and not args.no_big:
+        big = precision_comparison(tdh, args, flush, stream, world, rank)
 
     # end to end through the public API: pinned host in, host out, every step
     hx = {k: alpha.astype(np.float32) for k in KINDS}
@@ -452,10 +503,11 @@ def main():
             "error_vs_oracle": err,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": profile_traffic(),
-                         "peak_note": "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x max SM clock (derived)"},
+                         "peak_note": f"FP32 FFMA {apeaks['note']}; {apeaks['sms']} SMs"},
             "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
                     "note": "8 algorithmic bytes per coefficient (fp32 in + out); of measured"},
             "fp64": fp64,
+            "fp32_vs_fp64_n2p20": big,
             "e2e": {"value": e2e_value, "unit": "coeffs/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
             # per direction: the execute kernel and the balanced-split fix-up (36 resident
@@ -489,8 +541,8 @@ def run_extra(args, rank, world, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    apeaks = arith_peaks(tdh)
+    fp32_peak = apeaks["fp32"]
     hbm_peak = peaks.get("hbm_gbs", 6649.7)
     w = args.workload
     t0 = time.perf_counter()
@@ -505,7 +557,7 @@ def run_extra(args, rank, world, local):
         fn = lambda: plan.execute(x, out=y)
         coeffs, dtype = n * B, "f64"
         flops = flops_per_vector(plan.K, 1024) * B
-        bound, peak, unit, pnote = "alu", 1.25, "TFLOP/s", "FP64 nominal 1.25 TFLOP/s (GB300 table)"
+        bound, peak, unit, pnote = "alu", apeaks["fp64"], "TFLOP/s", "FP64 DFMA " + apeaks["note"]
         config = {"workload": "leg2cheb n=1024 batch=1 fp64 tol=1e-15", "K": plan.K}
         check = lambda: {"leg2cheb": float(np.abs(y.cpu().numpy() - oracle.matvec(oracle.LEG2CHEB, None, alpha)).max() / np.abs(alpha).sum())}
         host_in = torch.from_numpy(alpha).pin_memory()
@@ -534,7 +586,7 @@ def run_extra(args, rank, world, local):
         coeffs, dtype = int(offs[-1]), "f32"
         Ls = [max(256, 1 << int(math.ceil(math.log2(max(2 * ((int(n) + 1) // 2) - 1, 1))))) for n in lengths]
         flops = sum(flops_per_vector(plan.K, L) for L in Ls)
-        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived"
+        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA " + apeaks["note"]
         config = {"workload": "ragged leg2cheb 4096 vectors, degrees log-uniform [64, 65536), fp32, one CUDA-graph launch",
                   "K": plan.K, "plan": PLAN32["leg2cheb"], "coefficients": coeffs}
         def check():
@@ -572,7 +624,7 @@ def run_extra(args, rank, world, local):
         coeffs, dtype = 2 * n * B, "f32"
         # both Jacobi steps: rank pairs packed, FFT length 2^21 (factor count from the plan)
         flops = 2 * flops_per_vector(pj.K, 1 << 21) / 2 * B
-        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived (Jacobi multi-pass part)"
+        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA " + apeaks["note"] + " (Jacobi multi-pass part)"
         config = {"workload": "jacobi (0.1,-0.3)->(0,0) + ultraspherical 0.25->1.25, n=2^20, batch=16, fp32 execute, fp64 plan, tol 1e-13",
                   "K_jacobi_max_step": pj.K}
         check = None
@@ -594,7 +646,7 @@ def run_extra(args, rank, world, local):
             (wgt * beta * beta).sum().backward()
         coeffs, dtype = n * B, "f32"
         flops = 2 * flops_per_vector(plan.K, 8192) * B
-        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA, derived"
+        bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA " + apeaks["note"]
         config = {"workload": "autograd leg2cheb n=8192 batch=1024 fp32: forward + loss + backward (adjoint kernel)",
                   "K": plan.K, "plan": PLAN32["leg2cheb"]}
         def check():

@@ -3,10 +3,10 @@
  *
  * Method: Townsend, Webb & Olver, "Fast polynomial transforms based on Toeplitz and Hankel
  * matrices" (arXiv:1604.07486).  A conversion matrix is split as A = D1 (T o H) D2 (Fig. 1
- * step 1, eq. (HadamardDecomposition)); the Hankel part H is compressed by pivoted Cholesky,
+ * step 1, Eq. (3)); the Hankel part H is compressed by pivoted Cholesky,
  * H ~ sum_r l_r l_r^T / a_r (Sec. 2.1, Fig. 2); and beta = A alpha is computed as
- * D1 sum_r D_{u_r} T D_{u_r} D2 alpha with u_r = l_r / sqrt(a_r) (eq. (Cdecomposition)),
- * each Toeplitz product by FFT (Sec. 1, "O(K) FFTs of size 2N-1").
+ * D1 sum_r D_{u_r} T D_{u_r} D2 alpha with u_r = l_r / sqrt(a_r) (Eq. (5)),
+ * each Toeplitz product by zero-padded FFTs of length about 2N (Sec. 1).
  *
  * Conventions for every entry point
  *   - Pointers named d_* or documented as "device" are CUDA device pointers on the current
@@ -35,8 +35,8 @@ extern "C" {
 #endif
 
 /* ---------------------------------------------------------------- kinds (basis pairs) */
-#define TDH_LEG2CHEB    0 /* Legendre -> Chebyshev, eq. (M), split eq. (Decomposition)       */
-#define TDH_CHEB2LEG    1 /* Chebyshev -> Legendre, eq. (FormulaL), split Sec. 5.1           */
+#define TDH_LEG2CHEB    0 /* Legendre -> Chebyshev, Eq. (2), split Eq. (7)       */
+#define TDH_CHEB2LEG    1 /* Chebyshev -> Legendre, Eq. (11), split Sec. 5.1           */
 #define TDH_ULTRA2ULTRA 2 /* ultraspherical C^(l1) -> C^(l2), Sec. 5.2, p = {l1, l2}          */
 #define TDH_JAC2JAC     3 /* Jacobi P^(a,b) -> P^(g,d), Sec. 5.3, p = {a, b, g, d}           */
 #define TDH_LAG2LAG     4 /* generalised Laguerre L^(a1) -> L^(a2), Sec. 5.4, p = {a1, a2}   */
@@ -79,11 +79,11 @@ typedef struct {
  *   a1  the split's generator sequences t, h and diagonals D1, D2 from their closed forms
  *       (Gamma ratios by an asymptotic series at large argument, Tricomi-Erdelyi);
  *   a2  pivoted Cholesky of H (Sec. 2.1, Fig. 2), stopping before the first pivot a_r with
- *       a_r <= tol * max(diag H) ("zero or sufficiently small"), at most kmax steps;
+ *       a_r <= tol * max(diag H) (a negligible pivot ends it, Sec. 2.1), at most kmax steps;
  *   a3  the spectrum of the Toeplitz symbol for each FFT length in use.
  * For TDH_CHEB2LEG the factorisation covers indices 1..n_max-1 and row 0 is applied directly
- * (Sec. 5.1).  tol > 0 is relative to the largest diagonal entry of H; the paper takes
- * "a small multiple of machine epsilon" of the arithmetic used.
+ * (Sec. 5.1).  tol > 0 is relative to the largest diagonal entry of H; Sec. 2.1 sets it
+ * near the unit roundoff of the arithmetic used.
  * With TDH_FLAG_TARGET, tol is instead the accuracy asked of each T o H step's truncation:
  * the factorisation pivots on the congruent W H W, w_j = sqrt(|D1_j D2_j|) (1 where zero;
  * the same A = D1 W^-1 (T o W H W) W^-1 D2, so the greedy pivot chases the residual that the
@@ -97,7 +97,7 @@ typedef struct {
  * rounding comes on top.  If no prefix meets tol, every computed term is kept.
  * Case dispatch (a plan is a chain of steps applied in order):
  *   ULTRA (l1, l2 > 0): integer l2 - l1 (Case 1): sparse factors S_l of
- *     eq. (sparseFactorization), or their inverses by back-substitution when l2 < l1;
+ *     Eq. (12), or their inverses by back-substitution when l2 < l1;
  *     |l2 - l1| > 1 not an integer (Case 3): whole steps with those factors until the
  *     difference is below one, then Case 2 (T o H).  Differences within 1e-14 (relative) of
  *     an integer count as integers.
@@ -181,7 +181,7 @@ int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max);
 
 /*
  * Execute schedules (no counterpart in the paper, which fixes no GPU geometry).  Each FFT of
- * the execute path (eq. (Cdecomposition), "O(K) FFTs of size 2N-1", Sec. 1) runs on one of
+ * the execute path (Eq. (5): K zero-padded FFT pairs of length about 2N, Sec. 1) runs on one of
  * several compiled schedules: local FFT length LC = 2^log2LC per CTA, C CTAs per vector (a
  * thread-block cluster for C <= 8, a multi-pass exchange through global memory above), local
  * radix R, NT threads per CTA, and MINB, the CTAs per SM its registers are capped for.  A
@@ -237,12 +237,43 @@ const char* tdh_last_error(void);
 int tdh_launch_count(int64_t* count);
 
 /*
+ * tdh_alloc_stats -- instrumentation (the paper has no counterpart): stats (host, 3 int64)
+ * receives, for this process, all devices and threads together:
+ *   stats[0]  device allocations the library has made (plan memory and execute scratch);
+ *   stats[1]  plan-memory blocks currently held (freed by tdh_plan_destroy);
+ *   stats[2]  execute-scratch blocks currently held (returned to the pool stream-ordered).
+ * Errors: INVALID_ARG (NULL stats).
+ */
+int tdh_alloc_stats(int64_t* stats);
+
+/*
+ * tdh_measure_fma_rate -- instrumentation (the paper has no counterpart): the fused
+ * multiply-add throughput of the current device in precision prec (TDH_FP32: FFMA,
+ * TDH_FP64: DFMA), counted as two flops per FMA, in TFLOP/s, written to *tflops (host).
+ * A kernel of independent FMA chains fills every SM; the best of three timed launches (CUDA
+ * events on `stream`, after one untimed) is reported.  These rates bound the execute
+ * kernels, whose FFTs are arithmetic-bound.  Synchronous; changes no device setting.
+ * Errors: INVALID_ARG, NOMEM, CUDA.
+ */
+int tdh_measure_fma_rate(int prec, double* tflops, void* stream);
+
+/*
+ * tdh_test_fail_alloc -- failure injection for tests (the paper has no counterpart): the k-th
+ * device allocation the library attempts from now on (k >= 1, counting plan memory and
+ * execute scratch, all threads) fails on the host as if the device were out of memory: the
+ * calling entry point returns TDH_ERR_NOMEM with a message, frees what it had allocated, and
+ * no CUDA allocation is attempted for it.  k = 0 cancels a pending failure.  Only the one
+ * allocation fails; later ones proceed normally.  Errors: INVALID_ARG (k < 0).
+ */
+int tdh_test_fail_alloc(int64_t k);
+
+/*
  * tdh_symbols -- step a1 on its own: the split A = D1 (T o H) D2 of `kind` for n
  * coefficients, in float64, written to device arrays
  *   t[n]       T_{j, j+m} = t[m]           (upper-triangular Toeplitz generator)
  *   h[2n-1]    H_{jk} = h[j + k]           (Hankel generator)
  *   d1[n], d2[n]                            (the diagonals)
- * following eq. (Decomposition) (LEG2CHEB), Sec. 5.1 (CHEB2LEG; h[0] = 1), Sec. 5.2 (ULTRA,
+ * following Eq. (7) (LEG2CHEB), Sec. 5.1 (CHEB2LEG; h[0] = 1), Sec. 5.2 (ULTRA,
  * Case 2, |l1 - l2| < 1) and Sec. 5.3 (JAC with b == d, Case 2).  p as in tdh_params.p.
  * Asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA.
  */
@@ -274,8 +305,8 @@ int tdh_pchol(const double* h, int64_t n, int64_t j0, double tol, int64_t kmax, 
  *     (about 0.5 MB, held by every GPU that loads the library until the process exits);
  *     n > 65536 returns TDH_ERR_INVALID_ARG with a message;
  *   - no cudaMalloc / cudaFree or allocating library call;
- *   - the first call on a device (with that device current) looks up the array's address
- *     and caches it; make that first call before any stream capture;
+ *   - every call looks up the array's address for the current device
+ *     (cudaGetSymbolAddress, which allocates nothing) and synchronises `stream`;
  *   - all calls on a device share the array: calls whose GPU work overlaps (other streams or
  *     host threads) race and must be serialised by the caller.
  */

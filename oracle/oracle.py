@@ -12,7 +12,7 @@ matrices" (arXiv:1604.07486).
   paper's order, in float64.  Reading of the garbled inner update of Fig. 2: step j is
   applied to the new column as l_r <- l_r - l_j (l_j)_{p_r} / a_j, which is what the
   prose of Sec. 2.1 describes (apply each earlier Cholesky step to column p_r).
-* ``pivoted_cholesky_full`` is the O(K N^2) full-update form, eq. (FirstCholeskyStep).
+* ``pivoted_cholesky_full`` is the O(K N^2) full-update form, Eq. (6).
 * ``jac2jac`` composes the Case-2 formula with the reflection of Sec. 5.3 when
   beta != delta (reading: P_k^(a,b)(x) = (-1)^k P_k^(b,a)(-x)).  The closed form of
   Sec. 5.3 holds for every parameter pair (its Gamma ratios come from recurrences, which
@@ -20,8 +20,10 @@ matrices" (arXiv:1604.07486).
   4 are the same formula.
 * ``jac2cheb`` / ``cheb2jac`` use T_k = P_k^(-1/2,-1/2) / P_k^(-1/2,-1/2)(1) (Sec. 5.3,
   end): a Jacobi (-1/2, -1/2) conversion and a diagonal scaling.
-* ``fast_matvec`` is the outline of Fig. 1 in float64 with numpy's FFT as the Toeplitz
-  step; it is a CPU timing reference only, never the parity truth.
+* ``fast_plan`` / ``fast_apply`` / ``fast_matvec`` are the outline of Fig. 1 in float64
+  with numpy's (or scipy's) FFT as the Toeplitz step: the CPU timing reference of the same
+  algorithm, pinned against the dense ``matvec`` within the truncation bound; never the
+  parity truth for the GPU path.
 * ``truncation_bound`` / ``target_rank`` / ``pivot_weights``: the accuracy-targeted choice of
   the rank (a reading, not in the paper): the PSD residual of the Fig. 2 factorisation bounds
   every entry of A - A_K; the factorisation may pivot on W H W (w = sqrt|d1 d2|), the same A.
@@ -152,7 +154,7 @@ def pivoted_cholesky(column, diag, tol, kmax=None):
     """Sec. 2.1, Fig. 2: rank-K approximation H ~ sum_r l_r l_r^T / a_r.
 
     column(p) -> H[:, p] (float64, length N); diag = diag(H).
-    Stops before step r when the pivot is "zero or sufficiently small": max(d) <= tol * d0
+    Stops before step r once the pivot is negligible (Sec. 2.1): max(d) <= tol * d0
     or the pivot entry a_r = (l_r)_{p_r} of the updated column <= tol * d0, where
     d0 = max(diag(H)).  (a_r is the diagonal entry of H^(r-1) that d approximates; the
     two differ only by rounding, and checking both keeps a_r > 0.)
@@ -181,7 +183,7 @@ def pivoted_cholesky(column, diag, tol, kmax=None):
 
 
 def pivoted_cholesky_full(H, tol, kmax=None):
-    """eq. (FirstCholeskyStep) applied repeatedly: H^(r) = H^(r-1) - H_{:,p} H_{p,:} / H_pp.
+    """Eq. (6) applied repeatedly: H^(r) = H^(r-1) - H_{:,p} H_{p,:} / H_pp.
 
     The O(K N^2) form that updates the whole matrix; same pivot and stop rule as
     ``pivoted_cholesky``.  Returns (ells, a, pivots) with l_r = H^(r-1)[:, p_r].
@@ -241,7 +243,7 @@ def truncation_bound(kind, params, n, u):
     The residual R = H - sum_{r<K'} u_r u_r^T of a pivoted Cholesky of a positive
     semidefinite H is positive semidefinite, so each 2 x 2 principal minor gives
     |R_jk| <= sqrt(d_j d_k) with d = diag(R).  A - A_K' = D1 (T o R) D2 on the Hankel block
-    (Sec. 2, eq. (HadamardDecomposition)), hence
+    (Sec. 2, Eq. (3)), hence
         |(A - A_K')_jk| <= max|t| * |d1_j| sqrt(d_j) * |d2_k| sqrt(d_k),
     and max_j |beta_K' - beta| <= B(K') ||alpha||_1 with
         B(K') = max|t| * max_j |d1_j| sqrt(d_j) * max_k |d2_k| sqrt(d_k).
@@ -319,27 +321,57 @@ def cheb2jac(x, a, b, rows=None):
     return jac2jac(x / s, -0.5, -0.5, a, b, rows=rows)
 
 
-# ---------------------------------------------------------------- CPU timing reference
+# ---------------------------------------------------------------- fast product (Fig. 1)
 
-def fast_matvec(kind, params, x, tol=1e-15):
-    """Fig. 1 outline in float64: split, pivoted Cholesky, v = D2 x, w = (T o H) v via
-    eq. (Cdecomposition) with numpy FFT Toeplitz products, beta = D1 w.  Row 0 of
-    Chebyshev-to-Legendre is applied directly (Sec. 5.1).  CPU timing reference only."""
-    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
-    n = x.shape[-1]
+def fast_plan(kind, params, n, tol=1e-15, target=None):
+    """Steps 1-2 of Fig. 1 in float64 for vectors of n coefficients: the split (Eq. (3)),
+    the Fig. 2 factors of H (relative tolerance ``tol``; or, with ``target``, the fewest terms
+    of the weighted factorisation whose truncation bound is <= target), and the spectrum of
+    the Toeplitz symbol for the zero-padded length L >= 2n - 1.  Row 0 of the Chebyshev-to-
+    Legendre and Jacobi Case-3 products is kept for a direct dot product (Sec. 5.1, 5.3)."""
     t, h, d1, d2 = split(kind, params, n)
-    u, _ = hankel_factors(kind, params, n, tol)
+    if target is None:
+        u, _ = hankel_factors(kind, params, n, tol)
+    else:
+        w = pivot_weights(kind, params, n)
+        u, _ = hankel_factors(kind, params, n, 1e-18, 128, weights=w)
+        ok = np.nonzero(truncation_bound(kind, params, n, u) <= target)[0]
+        u = u[: int(ok[0]) if len(ok) else len(u)]
     L = 1
     while L < 2 * n - 1:
         L *= 2
-    spec = np.conj(np.fft.rfft(t, L))
-    v = x * d2
+    row0 = entries(kind, params, n, 0, 1)[0] if first_index(kind, params) == 1 else None
+    return {"n": n, "L": L, "spec": np.conj(np.fft.rfft(t, L)), "u": u, "d1": d1, "d2": d2,
+            "row0": row0}
+
+
+def fast_apply(plan, x, workers=None):
+    """Steps 3-5 of Fig. 1: v = D2 x; w = sum_r u_r o T (u_r o v), each Toeplitz product by a
+    zero-padded real FFT of length L, multiplied by the conjugate spectrum of t (a
+    correlation, since T_jk = t_{k-j}); beta = D1 w, then row 0 directly where the plan keeps
+    it.  ``workers`` > 1 runs the FFTs on that many host threads (scipy.fft)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    n, L = plan["n"], plan["L"]
+    if workers and workers > 1:
+        import scipy.fft as sf
+        rfft = lambda a: sf.rfft(a, L, axis=-1, workers=workers)
+        irfft = lambda a: sf.irfft(a, L, axis=-1, workers=workers)
+    else:
+        rfft = lambda a: np.fft.rfft(a, L, axis=-1)
+        irfft = lambda a: np.fft.irfft(a, L, axis=-1)
+    v = x * plan["d2"]
     w = np.zeros_like(v)
-    for ur in u:
-        xr = v * ur
-        y = np.fft.irfft(np.fft.rfft(xr, L, axis=-1) * spec, L, axis=-1)[..., :n]
-        w += ur * y
-    beta = w * d1
-    if kind == CHEB2LEG:
-        beta[:, 0] = matvec(CHEB2LEG, None, x, rows=[0])[:, 0]
+    for ur in plan["u"]:
+        w += ur * irfft(rfft(v * ur) * plan["spec"])[..., :n]
+    beta = w * plan["d1"]
+    if plan["row0"] is not None:
+        beta[:, 0] = x @ plan["row0"]
     return beta
+
+
+def fast_matvec(kind, params, x, tol=1e-15, target=None):
+    """beta = A x by the fast algorithm of Fig. 1 in float64 (one Toeplitz-dot-Hankel step:
+    Leg<->Cheb, ultraspherical and Jacobi Case 2/3, Laguerre).  A CPU timing reference,
+    pinned against ``matvec`` within the truncation bound (tests/test_oracle_fast.py)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    return fast_apply(fast_plan(kind, params, x.shape[-1], tol, target), x)

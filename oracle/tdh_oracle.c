@@ -10,12 +10,12 @@
  * Hankel matrices" (arXiv:1604.07486).  The oracle is the paper's "Direct" algorithm
  * (Sec. 4): every entry A_jk is generated from its closed form and dotted with alpha,
  * O(n^2) work and O(n) memory.  The closed forms are
- *   LEG2CHEB   eq. (M)            M_jk
- *   CHEB2LEG   eq. (FormulaL)     L_jk
- *   ULTRA      eq. (UltraSconversion), Sec. 5.2
+ *   LEG2CHEB   Eq. (2)            M_jk
+ *   CHEB2LEG   Eq. (11)     L_jk
+ *   ULTRA      Eq. (13), Sec. 5.2
  *   JAC        the Jacobi formula of Sec. 5.3 (beta = delta), Cases 2 and 3
  *   LAG        the Laguerre formula of Sec. 5.4
- * together with the paper's diagonal/Toeplitz/Hankel split of each (eq. (Decomposition),
+ * together with the paper's diagonal/Toeplitz/Hankel split of each (Eq. (7),
  * Sec. 5.1, 5.2, 5.3), exported separately so that tests can check the split identity.
  *
  * Precision.  Every Gamma ratio the formulas need is produced by its first-order
@@ -26,10 +26,10 @@
  * fused multiply-add is used, so results are identical on x86-64 and aarch64 when built
  * with -ffp-contract=off.
  *
- * Reading where the paper is garbled: eq. (M) states the j = 0 row for "j even"; the
+ * Reading where the paper is garbled: Eq. (2) states the j = 0 row for "j even"; the
  * row is nonzero for k even (j = 0 is always even), which is what exact conversion
  * gives.  The ultraspherical T of Sec. 5.2 prints Gamma(lambda1-lambda2) in the
- * numerator; the reading that matches eq. (UltraSconversion) divides by it.
+ * numerator; the reading that matches Eq. (13) divides by it.
  */
 #include <math.h>
 #include <stdint.h>
@@ -153,7 +153,7 @@ typedef struct {
 } tables;
 
 /*
- * Lambda(z) = Gamma(z + 1/2) / Gamma(z + 1) at z = i/2 (eq. (M)).
+ * Lambda(z) = Gamma(z + 1/2) / Gamma(z + 1) at z = i/2 (Eq. (2)).
  * Integer z: Lambda(0) = sqrt(pi); half-integer z: Lambda(1/2) = Gamma(1)/Gamma(3/2) = 2/sqrt(pi).
  * Both chains advance by Lambda(z+1) = Lambda(z) (z + 1/2) / (z + 1).
  */
@@ -295,13 +295,13 @@ static inline dd entry(const tables* tb, int64_t j, int64_t k) {
     if (k < j) return zero;
     switch (tb->kind) {
     case K_LEG2CHEB: {
-        /* eq. (M): M_0k = Lambda(k/2)^2 / pi (k even); M_jk = 2/pi Lambda((k-j)/2) Lambda((k+j)/2). */
+        /* Eq. (2): M_0k = Lambda(k/2)^2 / pi (k even); M_jk = 2/pi Lambda((k-j)/2) Lambda((k+j)/2). */
         if ((k - j) & 1) return zero;
         if (j == 0) return dd_mul(tb->c_row0, dd_mul(tb->lam[k], tb->lam[k]));
         return dd_mul(tb->c_rest, dd_mul(tb->lam[k - j], tb->lam[k + j]));
     }
     case K_CHEB2LEG: {
-        /* eq. (FormulaL). */
+        /* Eq. (11). */
         if ((k - j) & 1) return zero;
         if (j == k) {
             if (j == 0) return dd_from(1.0);
@@ -314,7 +314,7 @@ static inline dd entry(const tables* tb, int64_t j, int64_t k) {
         return dd_mul(c, dd_mul(f1, f2));
     }
     case K_ULTRA: {
-        /* eq. (UltraSconversion): (j + l2) P'((k-j)/2) Q'((k+j)/2), k - j even. */
+        /* Eq. (13): (j + l2) P'((k-j)/2) Q'((k+j)/2), k - j even. */
         if ((k - j) & 1) return zero;
         dd c = dd_add(dd_from((double)j), dd_from(tb->prm[1]));
         return dd_mul(c, dd_mul(tb->P[(k - j) / 2], tb->Q[(k + j) / 2]));
@@ -407,7 +407,7 @@ int tdho_entries(int kind, const double* prm, int64_t n, int64_t j0, int64_t j1,
  *   t[m]  = T_{j, j+m}, m in [0, n)          (upper-triangular Toeplitz)
  *   h[s]  = H_{jk} with j + k = s, s in [0, 2n-1)
  *   d1[j], d2[k], j, k in [0, n)
- * LEG2CHEB   eq. (Decomposition): D1 = 2/pi diag(1/2, 1, ...), D2 = I,
+ * LEG2CHEB   Eq. (7): D1 = 2/pi diag(1/2, 1, ...), D2 = I,
  *            t_m = Lambda(m/2) (m even, else 0), h_s = Lambda(s/2).
  * CHEB2LEG   Sec. 5.1: D1 = diag(j + 1/2), D2 = -1/4 diag(4/sqrt(pi), 1, 2, ..., N),
  *            t_m = Gamma((m-1)/2)/Gamma((m+2)/2) (m even), h_s = Gamma(s/2)/Gamma((s+3)/2), h_0 = 1.

@@ -24,7 +24,8 @@ EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "t
            "tdh_plan_destroy", "tdh_last_error", "tdh_symbols", "tdh_pchol", "tdh_pchol_noalloc",
            "tdh_plan_execute_ragged", "tdh_launch_count", "tdh_plan_execute_host",
            "tdh_plan_schedule_count", "tdh_plan_schedule_info", "tdh_plan_set_schedule",
-           "tdh_plan_autotune", "tdh_schedules")
+           "tdh_plan_autotune", "tdh_schedules", "tdh_alloc_stats", "tdh_test_fail_alloc",
+           "tdh_measure_fma_rate")
 FLAG_RAGGED = 1
 FLAG_TARGET = 2
 
@@ -70,6 +71,9 @@ def lib():
         L.tdh_pchol.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
         L.tdh_pchol_noalloc.argtypes = [vp, i64, i64, dbl, i64, vp, vp, ctypes.POINTER(i64), vp]
         L.tdh_launch_count.argtypes = [ctypes.POINTER(i64)]
+        L.tdh_alloc_stats.argtypes = [ctypes.POINTER(i64)]
+        L.tdh_test_fail_alloc.argtypes = [i64]
+        L.tdh_measure_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(dbl), vp]
         L.tdh_plan_execute_host.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
         L.tdh_plan_schedule_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.tdh_plan_schedule_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -267,3 +271,25 @@ def launch_count():
     c = ctypes.c_int64()
     _check(lib().tdh_launch_count(ctypes.byref(c)))
     return int(c.value)
+
+
+def alloc_stats():
+    """(allocations made, plan blocks held, scratch blocks held) (tdh_alloc_stats)."""
+    c = (ctypes.c_int64 * 3)()
+    _check(lib().tdh_alloc_stats(c))
+    return tuple(int(v) for v in c)
+
+
+def inject_alloc_failure(k):
+    """Make the k-th device allocation of the library from now on fail with NOMEM
+    (tdh_test_fail_alloc; k = 0 cancels)."""
+    _check(lib().tdh_test_fail_alloc(int(k)))
+
+
+def measure_fma_rate(prec, stream=None):
+    """FMA throughput of the current device in TFLOP/s (tdh_measure_fma_rate): prec "fp32"
+    (FFMA) or "fp64" (DFMA), two flops per FMA."""
+    prec = PRECS[prec] if isinstance(prec, str) else int(prec)
+    v = ctypes.c_double()
+    _check(lib().tdh_measure_fma_rate(prec, ctypes.byref(v), _stream(stream)))
+    return float(v.value)

@@ -15,7 +15,21 @@ namespace tdh {
 namespace {
 thread_local char g_err[1024];
 std::atomic<int64_t> g_launches{0};
+// allocation bookkeeping (tdh_alloc_stats) and the test hook that makes one fail
+std::atomic<int64_t> g_allocs{0};         // device allocations made (plan + scratch)
+std::atomic<int64_t> g_dev_live{0};       // plan blocks (dev_alloc) not yet freed
+std::atomic<int64_t> g_scratch_live{0};   // scratch blocks (scratch_alloc) not yet freed
+std::atomic<int64_t> g_fail_countdown{0}; // > 0: the allocation that brings it to 0 fails
+
+// True when the test hook says this allocation is the one to fail.
+bool injected_failure() {
+    int64_t k = g_fail_countdown.load();
+    while (k > 0) {
+        if (g_fail_countdown.compare_exchange_weak(k, k - 1)) return k == 1;
+    }
+    return false;
 }
+}  // namespace
 
 void note_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
@@ -31,6 +45,11 @@ void clear_error() { g_err[0] = '\0'; }
 int dev_alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (injected_failure()) {
+        set_error("cudaMalloc(%zu bytes): out of memory (failure injected by "
+                  "tdh_test_fail_alloc)", bytes);
+        return TDH_ERR_NOMEM;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -38,11 +57,15 @@ int dev_alloc(void** p, size_t bytes) {
         set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? TDH_ERR_NOMEM : TDH_ERR_CUDA;
     }
+    g_allocs.fetch_add(1);
+    g_dev_live.fetch_add(1);
     return TDH_OK;
 }
 
 void dev_free(void* p) {
-    if (p) cudaFree(p);
+    if (!p) return;
+    cudaFree(p);
+    g_dev_live.fetch_sub(1);
 }
 
 // Execute-time scratch comes from one library-owned memory pool per device whose release
@@ -75,6 +98,11 @@ int scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
         }
         pool = pools[dev];
     }
+    if (injected_failure()) {
+        set_error("scratch allocation of %zu bytes: out of memory (failure injected by "
+                  "tdh_test_fail_alloc)", bytes);
+        return TDH_ERR_NOMEM;
+    }
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -82,12 +110,24 @@ int scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
         set_error("scratch allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? TDH_ERR_NOMEM : TDH_ERR_CUDA;
     }
+    g_allocs.fetch_add(1);
+    g_scratch_live.fetch_add(1);
     return TDH_OK;
 }
 
 void scratch_free(void* p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    cudaFreeAsync(p, s);
+    g_scratch_live.fetch_sub(1);
 }
+
+void alloc_stats(int64_t* out) {
+    out[0] = g_allocs.load();
+    out[1] = g_dev_live.load();
+    out[2] = g_scratch_live.load();
+}
+
+void fail_alloc_after(int64_t k) { g_fail_countdown.store(k > 0 ? k : 0); }
 
 int sm_count() {
     int dev = 0, n = 0;
@@ -456,6 +496,26 @@ int tdh_launch_count(int64_t* count) {
         return TDH_ERR_INVALID_ARG;
     }
     *count = g_launches.load(std::memory_order_relaxed);
+    return TDH_OK;
+}
+
+int tdh_alloc_stats(int64_t* stats) {
+    tdh::clear_error();
+    if (!stats) {
+        tdh::set_error("tdh_alloc_stats: NULL stats");
+        return TDH_ERR_INVALID_ARG;
+    }
+    tdh::alloc_stats(stats);
+    return TDH_OK;
+}
+
+int tdh_test_fail_alloc(int64_t k) {
+    tdh::clear_error();
+    if (k < 0) {
+        tdh::set_error("tdh_test_fail_alloc: k must be >= 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    tdh::fail_alloc_after(k);
     return TDH_OK;
 }
 

@@ -1,5 +1,5 @@
 // Steps a4-a7: the fused execute kernel, beta = D1 sum_r u_r o T (u_r o D2 alpha)
-// (Fig. 1 steps 3-5, eq. (Cdecomposition)), and its adjoint.
+// (Fig. 1 steps 3-5, Eq. (5)), and its adjoint.
 //
 // Layout.  T has the parity structure of the Legendre/Chebyshev/ultraspherical cases
 // (T_jk = 0 for k - j odd), so even and odd indices never mix: with z_a = x_{2a} + i x_{2a+1}

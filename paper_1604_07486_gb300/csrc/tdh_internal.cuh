@@ -44,6 +44,10 @@ int scratch_alloc(void** p, size_t bytes, cudaStream_t s);
 void scratch_free(void* p, cudaStream_t s);
 
 int sm_count();
+// Allocation bookkeeping: {allocations made, plan blocks live, scratch blocks live}; and the
+// test hook that makes the k-th allocation from now fail (k = 0: none).
+void alloc_stats(int64_t* out);
+void fail_alloc_after(int64_t k);
 
 // One-time set-up per device (kernel attributes, occupancy queries): `f(int* val)` returns a
 // cudaError_t and runs once for each device that is current when it is needed; its result

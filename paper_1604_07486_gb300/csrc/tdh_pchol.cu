@@ -17,7 +17,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "tdh_internal.cuh"
@@ -358,12 +357,13 @@ extern "C" int tdh_pchol(const double* h, int64_t n, int64_t j0, double tol, int
 // sized device array that lives in this file.  The array is part of the library image: every
 // GPU that loads the library holds it until the process exits.
 //
-// Set-up: the first call on a device (with that device current) looks up the array's device
-// address with cudaGetSymbolAddress and caches it per device; make that first call before any
-// stream capture.  All calls on a device share the one array and it keeps the contents of the
-// last call: the state words that must start at zero are cleared by every call, the rest is
-// fully rewritten.  Two calls whose work overlaps on the GPU (different streams, or different
-// host threads) race on the array; serialise them.
+// Every call looks up the array's device address for the current device with
+// cudaGetSymbolAddress (a lookup, not an allocation) and passes it to the kernels, so the
+// address is always the one of the current context.  All calls on a device share the one
+// array and it keeps the contents of the last call: the state words that must start at zero
+// are cleared by every call, the rest is fully rewritten.  Two calls whose work overlaps on
+// the GPU (different streams, or different host threads) race on the array; serialise them.
+// Each call synchronises `stream` (it reads the stop state back every few steps).
 namespace tdh {
 namespace {
 
@@ -375,28 +375,14 @@ constexpr size_t kNoAllocBytes = kNoAllocDBytes + kNoAllocPartBytes + 256;
 
 static __device__ __align__(256) unsigned char g_pchol_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 int noalloc_scratch(unsigned char** out) {
-    int dev = 0;
-    TDH_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("tdh_pchol_noalloc: device index %d out of range", dev);
-        return TDH_ERR_UNSUPPORTED;
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_pchol_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("tdh_pchol_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return TDH_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_pchol_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("tdh_pchol_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            return TDH_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = p;
-    }
-    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    *out = static_cast<unsigned char*>(p);
     return TDH_OK;
 }
 
@@ -426,7 +412,9 @@ extern "C" int tdh_pchol_noalloc(const double* h, int64_t n, int64_t j0, double 
     State* st = reinterpret_cast<State*>(base + kNoAllocDBytes + kNoAllocPartBytes);
     if (kmax > kKmaxShared) kmax = kKmaxShared;
     if (kmax > n - j0) kmax = n - j0;
-    const int nblk = (int)std::max<int64_t>(1, (n + kThreads - 1) / kThreads);
+    // the same grid as tdh_pchol (at most 4 blocks per SM), within the array's partials
+    int nblk = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 4 * (int64_t)sm_count());
+    if (nblk < 1) nblk = 1;
     State host{0.0, 0, 0};
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(State), s);
     if (e == cudaSuccess) {

@@ -1,6 +1,6 @@
 // Case 1 of the ultraspherical (Sec. 5.2) and Jacobi (Sec. 5.3) conversions: when the two
 // parameters differ by an integer, A is a product of sparse upper-triangular factors, each
-// applied in O(n) (eq. (sparseFactorization) and its Jacobi analogue).  A factor is
+// applied in O(n) (Eq. (12) and its Jacobi analogue).  A factor is
 //   (S c)_j = p_j c_j + q_j c_{j+off}
 // with
 //   ultraspherical S_l (C^(l) -> C^(l+1)), off = 2:  p_j = l/(l+j),  q_j = -l/(l+j+2);

@@ -165,7 +165,7 @@ int symbols_launch(int kind, int64_t n, const double* p, double* t, double* h, d
     int64_t nh = 2 * n - 1;
     switch (kind) {
     case TDH_LEG2CHEB: {
-        // eq. (Decomposition): T = Lambda((k-j)/2) for k-j even, H = Lambda((j+k)/2),
+        // Eq. (7): T = Lambda((k-j)/2) for k-j even, H = Lambda((j+k)/2),
         // D1 = 2/pi diag(1/2, 1, ..., 1), D2 = I; Lambda(z) = Gamma(z+1/2)/Gamma(z+1).
         TableSpec ts = ratio_spec(0.5, 1.0, 0.0, 0.5, 1.0);
         ts.even_only = 1;

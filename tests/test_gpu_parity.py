@@ -269,8 +269,8 @@ def test_jacobi_adjoint(tdh):
                          ids=["case1", "case1_two_factors", "case3", "case3_two_steps"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_ultraspherical_case1_case3(tdh, params, prec):
-    """Sec. 5.2 Case 1 (sparse factors of eq. (sparseFactorization)) and Case 3 (whole steps,
-    then Case 2) against the dense oracle (eq. (UltraSconversion) covers every case)."""
+    """Sec. 5.2 Case 1 (sparse factors of Eq. (12)) and Case 3 (whole steps,
+    then Case 2) against the dense oracle (Eq. (13) covers every case)."""
     n = 4099
     tol = 1e-15 if prec == "fp64" else 1e-8
     plan, alpha, y = _run(tdh, "ultra2ultra", n, 3, prec, tol, decay=1.5, params=params)
@@ -384,6 +384,32 @@ def test_config4_jacobi_n2p20_b16(tdh):
     ref2 = np.stack([oracle.jac2jac(v[:8192], *params) for v in a2])
     err = (np.abs(y2[:, :8192] - ref2).max(axis=1) / np.abs(a2).sum(axis=1)).max()
     assert err <= 5e-6, err
+
+
+@pytest.mark.parametrize("kind,params,prec", [
+    ("jac2jac", (0.1, -0.3, 0.0, -0.3), "fp32"),
+    ("jac2jac", (0.1, -0.3, 0.0, -0.3), "fp64"),
+    ("leg2cheb", None, "fp32"),
+], ids=["jacobi-fp32", "jacobi-fp64", "leg2cheb-fp32"])
+def test_multipass_middle_rows_n2p20(tdh, kind, params, prec):
+    """A single Case-2 step at n = 2^20 (multi-pass FFTs: 2^21 points in 256 slices for the
+    rank-pair-packed Jacobi step, 2^20 in 128 for Legendre -> Chebyshev), batch 2, against the
+    dense oracle on 320 rows spread over the whole vector: rows in the middle of every slice
+    and of the cross-slice exchange, not only the tail."""
+    torch = _torch()
+    n, batch = 1 << 20, 2
+    alpha = workloads.coefficients(n, batch, decay=1.5, seed=31)
+    tol = 5e-6 if prec == "fp32" else 1e-12
+    plan = tdh.Plan(kind, n, prec=prec, params=params or ())
+    y = plan.execute(torch.tensor(alpha, dtype=plan.dtype, device="cuda")).double().cpu().numpy()
+    rng = np.random.default_rng(32)
+    rows = np.unique(np.r_[np.arange(32), n - 1 - np.arange(32), rng.integers(0, n, 256)])
+    if kind == "jac2jac":
+        ref = oracle.matvec(oracle.JAC, params[:3], alpha, rows=rows)
+    else:
+        ref = oracle.matvec(oracle.LEG2CHEB, None, alpha, rows=rows)
+    err = (np.abs(y[:, rows] - ref).max(axis=1) / np.abs(alpha).sum(axis=1)).max()
+    assert err <= tol, (err, plan.K)
 
 
 def test_config4_supplementary_ultraspherical_case2_n2p20(tdh):

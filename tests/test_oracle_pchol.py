@@ -50,7 +50,7 @@ def test_rank_at_N300_reaches_double_precision_within_paper_steps():
                                          (oracle.ULTRA, (0.75, 1.25)), (oracle.JAC, (0.1, -0.3, 0.0))])
 def test_matches_full_update_form(kind, params):
     """The O(K^2 N) column form (Fig. 2, reading of its inner update) equals the O(K N^2)
-    full-update form, eq. (FirstCholeskyStep): same pivots, same columns."""
+    full-update form, Eq. (6): same pivots, same columns."""
     H = _H(kind, params, 200)
     e1, a1, p1 = oracle.pivoted_cholesky(lambda p: H[:, p], np.diag(H), 1e-14)
     e2, a2, p2 = oracle.pivoted_cholesky_full(H, 1e-14)
@@ -104,7 +104,7 @@ def test_residual_bounded_by_tolerance(kind, params):
 
 def test_garbled_update_is_rejected():
     """Taken literally, Fig. 2's printed update l_r <- l_r - l_j (l_r)_j / (l_r)_{p_r} does
-    not reproduce eq. (FirstCholeskyStep); the comparison above would catch it."""
+    not reproduce Eq. (6); the comparison above would catch it."""
     H = _H(oracle.LEG2CHEB, None, 120)
     d = np.diag(H).copy()
     ells, piv = [], []
@@ -124,7 +124,7 @@ def test_garbled_update_is_rejected():
 @pytest.mark.parametrize("mutation", ["transpose", "row0_factor", "sign", "shift"])
 def test_exact_pin_catches_planted_mistakes(mutation):
     """Plausible mistakes in the closed form (a transposed operand, the row-0 factor of
-    eq. (M) dropped, a sign flip, an index shift) fail the exact-rational comparison."""
+    Eq. (2) dropped, a sign flip, an index shift) fail the exact-rational comparison."""
     n = 12
     exact = polys.to_float(polys.conversion(polys.family("legendre", n), polys.family("chebyshev", n)))
     A = oracle.entries(oracle.LEG2CHEB, None, n)

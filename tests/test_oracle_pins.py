@@ -49,7 +49,7 @@ def _exact(src, dst, n):
 
 @pytest.mark.parametrize("name,kind,params,src,dst", CASES, ids=[c[0] for c in CASES])
 def test_entries_match_exact_conversion(name, kind, params, src, dst):
-    """Closed-form entries (eq. (M), (FormulaL), (UltraSconversion), Sec. 5.3, 5.4) equal the
+    """Closed-form entries (Eqs. (2), (11), (13), Sec. 5.3, 5.4) equal the
     exact conversion matrix from the polynomial recurrences, to a few ulp."""
     n = 12
     exact = polys.to_float(_exact(src, dst, n))
@@ -63,7 +63,7 @@ def test_entries_match_exact_conversion(name, kind, params, src, dst):
 @pytest.mark.parametrize("name,kind,params,src,dst", [c for c in CASES if c[1] != oracle.LAG],
                          ids=[c[0] for c in CASES if c[1] != oracle.LAG])
 def test_split_identity(name, kind, params, src, dst):
-    """A = D1 (T o H) D2 with the paper's split (eq. (Decomposition), Sec. 5.1-5.3)
+    """A = D1 (T o H) D2 with the paper's split (Eq. (7), Sec. 5.1-5.3)
     reproduces the exact matrix; for Chebyshev-to-Legendre on indices j, k >= 1 only,
     since Sec. 5.1 applies row 0 directly."""
     n = 12
@@ -79,8 +79,8 @@ def test_split_identity(name, kind, params, src, dst):
 
 
 def test_worked_constants():
-    """P_2 = 3/4 T_2 + 1/4 T_0 gives M_00 = 1, M_11 = 1, M_02 = 1/4, M_22 = 3/4 (eq. (M));
-    T_2 = 4/3 P_2 - 1/3 P_0 gives L_02 = -1/3, L_22 = 4/3 (eq. (FormulaL))."""
+    """P_2 = 3/4 T_2 + 1/4 T_0 gives M_00 = 1, M_11 = 1, M_02 = 1/4, M_22 = 3/4 (Eq. (2));
+    T_2 = 4/3 P_2 - 1/3 P_0 gives L_02 = -1/3, L_22 = 4/3 (Eq. (11))."""
     vals = {}
     with open(os.path.join(GOLDEN, "worked_entries.txt")) as f:
         for line in f:
@@ -179,7 +179,7 @@ def _gauss_jacobi_01(npts, a, b):
 
 def test_hankel_moment_integrals():
     """The Hankel generators are moments of the measures the paper gives (Thm 3.2, Sec. 5.1,
-    5.2, eq. (HankelPosDefJacobi)); evaluated by Gauss-Jacobi quadrature, not Gamma ratios."""
+    5.2, Eq. (15)); evaluated by Gauss-Jacobi quadrature, not Gamma ratios."""
     from math import gamma, pi, sqrt
     n = 40
     s = np.arange(2 * n - 1)
@@ -273,7 +273,7 @@ def _bidiagonal(n, off, diag, sup):
 def test_sparse_factor_readings():
     """The sparse factors the GPU path applies for integer steps, checked exactly.
 
-    Sec. 5.2, eq. (sparseFactorization): (S_l)_jj = l/(l+j), (S_l)_{j,j+2} = -l/(l+j+2) maps
+    Sec. 5.2, Eq. (12): (S_l)_jj = l/(l+j), (S_l)_{j,j+2} = -l/(l+j+2) maps
     C^(l) coefficients to C^(l+1) coefficients.  Sec. 5.3 Case 1: S_(a,b) maps (a, b)
     coefficients to (a+1, b) coefficients with diagonal (j+a+b+1)/(2j+a+b+1) (1 at j = 0)
     and superdiagonal -(j+b+1)/(2j+a+b+3).  The paper prints the superdiagonal numerator

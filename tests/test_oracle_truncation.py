@@ -2,7 +2,7 @@
 
 The bound rests on one fact about the pivoted Cholesky of Sec. 2.1 (Fig. 2): the residual
 R = H - sum_{r<K} u_r u_r^T of a positive semidefinite H is positive semidefinite, so
-|R_jk| <= sqrt(d_j d_k).  Through A = D1 (T o H) D2 (eq. (HadamardDecomposition)) every entry
+|R_jk| <= sqrt(d_j d_k).  Through A = D1 (T o H) D2 (Eq. (3)) every entry
 of A - A_K is then at most max|t| |d1_j| sqrt(d_j) |d2_k| sqrt(d_k).  These tests check the
 bound against the dense error of every prefix, by brute force on small n, and show that
 plausible slips in writing it down are caught.
