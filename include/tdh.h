@@ -46,6 +46,13 @@ extern "C" {
 /* ---------------------------------------------------------------- execute precisions */
 #define TDH_FP64  0 /* float64 in/out, float64 FFT                                             */
 #define TDH_FP32  1 /* float32 in/out, float32 FFT (plan factors rounded once from float64)    */
+/* float32 in/out; within one thread-block cluster (FFTs of up to 2^17 points) the radix-16
+ * (radix-8 for short FFTs) middle passes of every FFT run on the tensor cores as DFT matrix
+ * products in split bfloat16: each operand x = hi + lo (bfloat16 parts) and the three products
+ * hi*hi + lo*hi + hi*lo accumulate in float32 (tcgen05, tensor memory); every other pass and
+ * the multi-pass FFTs beyond one cluster are float32.  The split keeps about 16 bits of each
+ * operand, so errors are larger than TDH_FP32's.                                              */
+#define TDH_BF16X3 2
 
 /* ---------------------------------------------------------------- plan flags */
 #define TDH_FLAG_NONE   0
@@ -58,9 +65,14 @@ extern "C" {
 #define TDH_ERR_UNSUPPORTED (-2) /* valid request this build does not implement            */
 #define TDH_ERR_NOMEM       (-3) /* device or host allocation failed                       */
 #define TDH_ERR_ALIGN       (-4) /* pointer not aligned to 16 bytes                         */
-#define TDH_ERR_TIMEOUT     (-5) /* reserved (no entry point of this build waits on the GPU) */
+#define TDH_ERR_TIMEOUT     (-5) /* reserved (device-side waits report through tdh_plan_status) */
 #define TDH_ERR_CUDA        (-6) /* a CUDA runtime call failed (message has the detail)     */
 #define TDH_ERR_ALIAS       (-7) /* out overlaps in where the operation forbids it          */
+
+/* ---------------------------------------------------------------- device status bits */
+#define TDH_STATUS_TIMEOUT 1 /* a tensor-core pass's bounded wait for its products ran out  */
+#define TDH_STATUS_LENGTH  2 /* a ragged vector was longer than n_max (or offsets decreased) */
+#define TDH_STATUS_ALIAS   4 /* a ragged call's out range overlapped its in range          */
 
 /* opaque; after creation only tdh_plan_set_schedule and tdh_plan_autotune change it */
 typedef struct tdh_plan_s* tdh_plan_t;
@@ -68,7 +80,7 @@ typedef struct tdh_plan_s* tdh_plan_t;
 typedef struct {
     double p[4];  /* kind parameters: ULTRA {l1, l2}; JAC {a, b, g, d}; LAG {a1, a2};
                      JAC2CHEB / CHEB2JAC {a, b}                                              */
-    int prec;     /* TDH_FP64 or TDH_FP32: the precision of plan_execute's in/out and FFTs  */
+    int prec;     /* TDH_FP64, TDH_FP32 or TDH_BF16X3: execute in/out type, FFT arithmetic  */
     int flags;    /* TDH_FLAG_NONE, or TDH_FLAG_RAGGED and/or TDH_FLAG_TARGET (bitwise or)    */
     int64_t kmax; /* cap on the rank of each Hankel factorisation; 0 selects 128            */
 } tdh_params;
@@ -133,11 +145,14 @@ int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, 
  * tdh_plan_execute_ragged -- beta = A alpha for `batch` vectors of different lengths in one
  * call.  Vector v occupies in[offsets[v] .. offsets[v+1]) and its result the same range of
  * out; its length n_v = offsets[v+1] - offsets[v] must be <= n_max (longer vectors are left
- * unwritten; n_v = 0 is allowed).  One plan serves every length: H and T depend only on j+k
+ * unwritten and TDH_STATUS_LENGTH is recorded, see tdh_plan_status; n_v = 0 is allowed).  One plan serves every length: H and T depend only on j+k
  * and k-j, so the n_v-prefix of the n_max factors approximates the n_v problem within the same
  * tolerance (the residual of a principal submatrix is a principal submatrix of the residual).
  * in, out: device arrays of offsets[batch] values of the plan's precision; out must not
- * overlap in (not checked).  offsets: device, batch + 1 int64, non-decreasing, offsets[0] >= 0.
+ * overlap in.  The offsets live on the device, so that check runs there: if the ranges
+ * [offsets[0], offsets[batch]) of in and out overlap, nothing is converted and
+ * TDH_STATUS_ALIAS is recorded (tdh_plan_status); in == out is rejected on the host
+ * (TDH_ERR_ALIAS).  offsets: device, batch + 1 int64, non-decreasing, offsets[0] >= 0.
  * The plan must have been created with TDH_FLAG_RAGGED (else TDH_ERR_INVALID_ARG) and have a
  * single T o H conversion step (Legendre/Chebyshev/ultraspherical Case 2; plan creation with
  * the flag returns UNSUPPORTED for other chains) with FFT lengths within
@@ -222,6 +237,17 @@ int tdh_plan_autotune(tdh_plan_t plan, int64_t batch, void* stream);
 /* tdh_plan_destroy -- free the plan's device and host memory.  NULL is a no-op.  Waits for
  * nothing: the caller must not destroy a plan with launches still in flight. */
 int tdh_plan_destroy(tdh_plan_t plan);
+
+/*
+ * tdh_plan_status -- conditions the plan's kernels found on the device: *status (host)
+ * receives the TDH_STATUS_* bits recorded by the plan's executes so far (any stream), which
+ * are then cleared.  TIMEOUT: a split-bfloat16 kernel gave up waiting (after about one
+ * second) for its tensor-core products, and the outputs of that execute are not valid.
+ * LENGTH, ALIAS: see tdh_plan_execute_ragged.  Synchronises `stream`; executes of interest
+ * must be complete before it (e.g. enqueued on the same stream).
+ * Errors: INVALID_ARG (NULL plan or status), CUDA.
+ */
+int tdh_plan_status(tdh_plan_t plan, int* status, void* stream);
 
 /* tdh_last_error -- message of the last failing call on this thread ("" if none). */
 const char* tdh_last_error(void);

@@ -12,10 +12,10 @@ import os
 from . import build as _build
 
 LEG2CHEB, CHEB2LEG, ULTRA2ULTRA, JAC2JAC, LAG2LAG, JAC2CHEB, CHEB2JAC = 0, 1, 2, 3, 4, 5, 6
-FP64, FP32 = 0, 1
+FP64, FP32, BF16X3 = 0, 1, 2
 KINDS = {"leg2cheb": LEG2CHEB, "cheb2leg": CHEB2LEG, "ultra2ultra": ULTRA2ULTRA,
          "jac2jac": JAC2JAC, "lag2lag": LAG2LAG, "jac2cheb": JAC2CHEB, "cheb2jac": CHEB2JAC}
-PRECS = {"fp64": FP64, "fp32": FP32}
+PRECS = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
 ERRORS = {0: "OK", -1: "INVALID_ARG", -2: "UNSUPPORTED", -3: "NOMEM", -4: "ALIGN",
           -5: "TIMEOUT", -6: "CUDA", -7: "ALIAS"}
 
@@ -25,7 +25,7 @@ EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "t
            "tdh_plan_execute_ragged", "tdh_launch_count", "tdh_plan_execute_host",
            "tdh_plan_schedule_count", "tdh_plan_schedule_info", "tdh_plan_set_schedule",
            "tdh_plan_autotune", "tdh_schedules", "tdh_alloc_stats", "tdh_test_fail_alloc",
-           "tdh_measure_fma_rate")
+           "tdh_measure_fma_rate", "tdh_plan_status")
 FLAG_RAGGED = 1
 FLAG_TARGET = 2
 
@@ -74,6 +74,7 @@ def lib():
         L.tdh_alloc_stats.argtypes = [ctypes.POINTER(i64)]
         L.tdh_test_fail_alloc.argtypes = [i64]
         L.tdh_measure_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(dbl), vp]
+        L.tdh_plan_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
         L.tdh_plan_execute_host.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
         L.tdh_plan_schedule_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.tdh_plan_schedule_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -115,7 +116,8 @@ class Plan:
     vectors of n coefficients, built on the current CUDA device in float64.  tol is relative
     to max diag(H); with target=True it is the accuracy asked of the truncation instead
     (fewest rank terms whose residual bound gives max|beta_K - beta| <= tol ||alpha||_1).
-    Without tol the plan is accuracy-targeted at 2.5e-6 (float32) or 5e-13 (float64)."""
+    Without tol the plan is accuracy-targeted at half the precision's tolerance: 2.5e-6
+    (float32), 5e-6 (split bfloat16, "bf16x3") or 5e-13 (float64)."""
 
     def __init__(self, kind, n, prec="fp32", tol=None, params=(), kmax=0, ragged=False,
                  target=None):
@@ -123,8 +125,8 @@ class Plan:
         self.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
         if tol is None:
             # default: accuracy-targeted at half the precision's tolerance (5e-6 float32,
-            # 1e-12 float64, of ||alpha||_1), guaranteed for every input
-            tol = 5e-13 if self.prec == FP64 else 2.5e-6
+            # 1e-5 split bfloat16, 1e-12 float64, of ||alpha||_1), for every input
+            tol = {FP64: 5e-13, FP32: 2.5e-6, BF16X3: 5e-6}.get(self.prec, 2.5e-6)
             target = True if target is None else target
         target = bool(target)
         p = _Params()
@@ -144,7 +146,7 @@ class Plan:
     @property
     def dtype(self):
         torch = _torch()
-        return torch.float32 if self.prec == FP32 else torch.float64
+        return torch.float64 if self.prec == FP64 else torch.float32
 
     def close(self):
         if getattr(self, "_h", None):
@@ -200,6 +202,15 @@ class Plan:
     def adjoint(self, g, out=None, stream=None):
         """A^T g for every vector of g (the transpose product)."""
         return self._run(lib().tdh_plan_execute_adjoint, g, out, stream, adjoint=1)
+
+    STATUS = {1: "TIMEOUT", 2: "LENGTH", 4: "ALIAS"}
+
+    def status(self, stream=None):
+        """TDH_STATUS_* bits the plan's kernels recorded since the last call, then cleared
+        (tdh_plan_status; synchronises the stream): a set of names."""
+        v = ctypes.c_int()
+        _check(lib().tdh_plan_status(self._h, ctypes.byref(v), _stream(stream)))
+        return {name for bit, name in self.STATUS.items() if v.value & bit}
 
     _SCHED_KEYS = ("logL", "logLC", "C", "R", "NT", "MINB", "index", "count")
 

@@ -258,7 +258,7 @@ int run(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream,
         set_error("in/out must be 16-byte aligned");
         return TDH_ERR_ALIGN;
     }
-    const size_t esz = plan->params.prec == TDH_FP32 ? 4 : 8;
+    const size_t esz = plan->params.prec == TDH_FP64 ? 8 : 4;
     const size_t bytes = (size_t)batch * (size_t)plan->n_max * esz;
     if (overlaps(in, out, bytes)) {
         set_error("out overlaps in");
@@ -304,7 +304,7 @@ int run_host(tdh_plan_t plan, const void* h_in, void* h_out, int64_t batch, void
         set_error("NULL in/out");
         return TDH_ERR_INVALID_ARG;
     }
-    const size_t esz = plan->params.prec == TDH_FP32 ? 4 : 8;
+    const size_t esz = plan->params.prec == TDH_FP64 ? 8 : 4;
     const size_t vec_bytes = esz * (size_t)plan->n_max;
     if (overlaps(h_in, h_out, vec_bytes * (size_t)batch)) {
         set_error("out overlaps in");
@@ -535,7 +535,7 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         set_error("need n_max >= 1 and finite tol > 0");
         return TDH_ERR_INVALID_ARG;
     }
-    if (params->prec != TDH_FP32 && params->prec != TDH_FP64) {
+    if (params->prec != TDH_FP32 && params->prec != TDH_FP64 && params->prec != TDH_BF16X3) {
         set_error("unknown precision %d", params->prec);
         return TDH_ERR_INVALID_ARG;
     }
@@ -641,8 +641,16 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
         std::memcpy(st.p, p, sizeof(st.p));
         steps.push_back(st);
     }
+    if (rc == TDH_OK) {
+        rc = dev_alloc_t(&plan->status, 4);
+        if (rc == TDH_OK && cudaMemsetAsync(plan->status, 0, 4 * sizeof(int), s) != cudaSuccess) {
+            set_error("status word: cudaMemsetAsync failed");
+            rc = TDH_ERR_CUDA;
+        }
+    }
     for (auto& st : plan->steps) {
         if (rc != TDH_OK) break;
+        st.status = plan->status;
         rc = build_step(st, tol, (params->flags & TDH_FLAG_TARGET) ? 1 : 0, kmax, params->prec, s);
         if (rc != TDH_OK) break;
     }
@@ -682,6 +690,7 @@ int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double to
     cudaStreamDestroy(s);
     if (rc != TDH_OK) {
         for (auto& x : plan->steps) release_step(x);
+        dev_free(plan->status);
         destroy_plan_streams(plan);
         delete plan;
         return rc;
@@ -705,6 +714,10 @@ int tdh_plan_execute_ragged(tdh_plan_t plan, const void* in, void* out, const in
     if (!in || !out || !offsets) {
         set_error("NULL in/out/offsets");
         return TDH_ERR_INVALID_ARG;
+    }
+    if (in == out) {
+        set_error("out overlaps in");
+        return TDH_ERR_ALIAS;
     }
     if (!(plan->params.flags & TDH_FLAG_RAGGED) || plan->steps.size() != 1 ||
         plan->steps[0].rcls.empty()) {
@@ -749,7 +762,8 @@ int tdh_plan_query(tdh_plan_t plan, int64_t* K, int64_t* n_max) {
 
 int tdh_schedules(int prec, int logL, int ragged, int* out, int cap, int* count) {
     clear_error();
-    if ((prec != TDH_FP32 && prec != TDH_FP64) || logL < 1 || logL > 62 || cap < 0 || !count ||
+    if ((prec != TDH_FP32 && prec != TDH_FP64 && prec != TDH_BF16X3) || logL < 1 || logL > 62 ||
+        cap < 0 || !count ||
         (cap > 0 && !out)) {
         set_error("tdh_schedules: need a known precision, 1 <= logL <= 62, cap >= 0, non-NULL");
         return TDH_ERR_INVALID_ARG;
@@ -806,8 +820,24 @@ int tdh_plan_destroy(tdh_plan_t plan) {
     clear_error();
     if (!plan) return TDH_OK;
     for (auto& st : plan->steps) release_step(st);
+    dev_free(plan->status);
     destroy_plan_streams(plan);
     delete plan;
+    return TDH_OK;
+}
+
+int tdh_plan_status(tdh_plan_t plan, int* status, void* stream) {
+    clear_error();
+    if (!plan || !status) {
+        set_error("tdh_plan_status: NULL plan or status");
+        return TDH_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = as_stream(stream);
+    int v = 0;
+    TDH_CUDA(cudaMemcpyAsync(&v, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TDH_CUDA(cudaMemsetAsync(plan->status, 0, sizeof(int), s));
+    TDH_CUDA(cudaStreamSynchronize(s));
+    *status = v;
     return TDH_OK;
 }
 

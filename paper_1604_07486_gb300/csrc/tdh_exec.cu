@@ -12,16 +12,19 @@ namespace {
 // Threads and occupancy of the multi-pass kernels for local length 2^logLC: slices one below
 // the shared-memory cap run 256 threads, two CTAs per SM; full slices 512 threads, one CTA.
 void mp_threads(int prec, int logLC, int* NT, int* MINB) {
-    const int cap = (prec == TDH_FP32) ? 14 : 13;
+    const int cap = (prec != TDH_FP64) ? 14 : 13;
     *NT = logLC == cap ? 512 : 256;
     *MINB = logLC == cap ? 1 : 2;
 }
 
-// Default FFT geometry for a transform of 2^logL points in precision `prec`.
+// Default FFT geometry for a transform of 2^logL points in precision `prec`.  Split-bfloat16
+// plans take the float32 geometry, with tensor-core passes within one cluster (the multi-pass
+// FFTs beyond it run the float32 kernels).
 bool choose_geometry(int prec, int logL, Geometry* g) {
     g->prec = prec;
     g->logL = logL;
-    const int cap = (prec == TDH_FP32) ? 14 : 13;  // largest local FFT held in shared memory
+    g->tc = 0;
+    const int cap = (prec != TDH_FP64) ? 14 : 13;  // largest local FFT held in shared memory
     if (logL <= cap) {
         g->logLC = logL;
         g->C = 1;
@@ -36,15 +39,16 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
         }
     }
     if (g->C > 512) return false;  // C > 8: multi-pass through global memory
-    g->R = radix_for(prec == TDH_FP32, g->logLC);
+    g->R = radix_for(prec != TDH_FP64, g->logLC);
     g->NT = std::min(512, (1 << g->logLC) / g->R);
     g->MINB = 1;
     if (g->C > 8) mp_threads(prec, g->logLC, &g->NT, &g->MINB);
+    g->tc = (prec == TDH_BF16X3 && g->C <= 8) ? 1 : 0;
     return true;
 }
 
 bool same_schedule(const Geometry& a, const Geometry& b) {
-    return a.logLC == b.logLC && a.C == b.C && a.NT == b.NT && a.MINB == b.MINB;
+    return a.logLC == b.logLC && a.C == b.C && a.NT == b.NT && a.MINB == b.MINB && a.tc == b.tc;
 }
 
 // Every schedule with a compiled kernel for 2^logL points, the default first: the cluster
@@ -59,21 +63,26 @@ std::vector<Geometry> schedule_candidates(int prec, int logL, bool ragged) {
         Geometry g = d;
         g.logLC = logLC;
         g.C = C;
-        g.R = radix_for(prec == TDH_FP32, logLC);
+        g.R = radix_for(prec != TDH_FP64, logLC);
         g.NT = NT;
         g.MINB = MINB;
+        g.tc = (prec == TDH_BF16X3 && C <= 8) ? 1 : 0;
         for (const Geometry& o : out)
             if (same_schedule(o, g)) return;
         out.push_back(g);
     };
-    const bool f32 = prec == TDH_FP32;
-    const int n = f32 ? SchedTable<true>::size : SchedTable<false>::size;
+    const bool f32 = prec != TDH_FP64;
+    const int n = prec == TDH_BF16X3 ? SchedTableTC::size
+                  : f32             ? SchedTable<true>::size
+                                    : SchedTable<false>::size;
     for (int i = 0; i < n; ++i) {
-        const Sched e = f32 ? SchedTable<true>::at(i) : SchedTable<false>::at(i);
+        const Sched e = prec == TDH_BF16X3 ? SchedTableTC::at(i)
+                        : f32              ? SchedTable<true>::at(i)
+                                           : SchedTable<false>::at(i);
         if (e.logLC + ilog2(e.C) == logL) add(e.logLC, e.C, e.NT, e.MINB);
     }
     if (!ragged) {
-        const int cap = f32 ? 14 : 13;
+        const int cap = f32 ? 14 : 13;  // (multi-pass kernels: float32 arithmetic for BF16X3)
         for (int lc = cap; lc >= cap - 1; --lc) {
             if (logL - lc < 4 || logL - lc > 9) continue;  // 16 ... 512 slices
             int NT, MINB;
@@ -353,6 +362,10 @@ int prepare_diagonals(Step& st, cudaStream_t s) {
 
 template <typename T>
 int dispatch(const Geometry& g, const ExecParams<T>& P, int64_t batch, cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (g.tc)
+            return P.ragged ? dispatch_ragged_tc(g, P, batch, s) : dispatch_dense_tc(g, P, batch, s);
+    }
     return P.ragged ? dispatch_ragged(g, P, batch, s) : dispatch_dense(g, P, batch, s);
 }
 
@@ -387,6 +400,7 @@ int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int a
     P.next = nullptr;
     P.batch = batch;
     P.partial = nullptr;
+    P.status = st.status;
     return dispatch<T>(ex.g, P, batch, s);
 }
 
@@ -402,7 +416,7 @@ int exec_prepare(Step& st, int prec, cudaStream_t s) {
                   (long long)st.n, logL);
         return TDH_ERR_UNSUPPORTED;
     }
-    if (prec == TDH_FP32) {
+    if (prec != TDH_FP64) {
         TDH_TRY(prepare_diagonals<float>(st, s));
         return prepare_typed<float>(st, ex, ex.g, nullptr, 0, s);
     }
@@ -440,7 +454,7 @@ int exec_prepare_ragged(Step& st, int prec, cudaStream_t s) {
         set_error("ragged batches are built for the parity-packed kinds");
         return TDH_ERR_UNSUPPORTED;
     }
-    if (prec == TDH_FP32) return prepare_ragged_typed<float>(st, prec, s);
+    if (prec != TDH_FP64) return prepare_ragged_typed<float>(st, prec, s);
     return prepare_ragged_typed<double>(st, prec, s);
 }
 
@@ -459,12 +473,23 @@ void exec_release(ExecData& ex) {
 
 namespace {
 
-// Group the vectors of a ragged batch by FFT length class (device side, any order).
+// Group the vectors of a ragged batch by FFT length class (device side, any order).  Checks
+// recorded in the plan's status word: the whole output range [offs[0], offs[batch]) of `out`
+// overlapping that of `in` (nothing is converted), and vectors longer than n_max or with
+// decreasing offsets (those are left unwritten).
 __global__ void k_classify(const int64_t* __restrict__ offs, int64_t batch, int64_t n_max,
-                           int ncls, int* __restrict__ count, int* __restrict__ list) {
+                           int ncls, int* __restrict__ count, int* __restrict__ list,
+                           const char* in, const char* out, int esz, int* status) {
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= batch) return;
+    const int64_t span = (offs[batch] - offs[0]) * esz;
+    const int64_t gap = in > out ? (int64_t)(in - out) : (int64_t)(out - in);
+    if (span > 0 && gap < span) {
+        if (i == 0 && status) atomicOr(status, TDH_STATUS_ALIAS);
+        return;
+    }
     const int64_t n = offs[i + 1] - offs[i];
+    if ((n < 0 || n > n_max) && status) atomicOr(status, TDH_STATUS_LENGTH);
     if (n <= 0 || n > n_max) return;  // nothing to do / outside the plan (documented)
     const int64_t m = (n + 1) / 2;
     int logL = 8;
@@ -504,6 +529,7 @@ ExecParams<T> ragged_params(const Step& st, const ExecData& ex, const void* in, 
     P.list = list;
     P.count = count;
     P.next = next;
+    P.status = st.status;
     return P;
 }
 
@@ -525,7 +551,9 @@ int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t
     int rc = TDH_OK;
     cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * 2 * ncls, s);
     if (e == cudaSuccess) {
-        k_classify<<<blocks_for(batch), kThreads, 0, s>>>(offs, batch, st.n, ncls, count, list);
+        k_classify<<<blocks_for(batch), kThreads, 0, s>>>(
+            offs, batch, st.n, ncls, count, list, static_cast<const char*>(in),
+            static_cast<const char*>(out), (int)sizeof(T), st.status);
         note_launches(1);
         e = cudaGetLastError();
     }
@@ -555,14 +583,14 @@ int launch_ragged_typed(const Step& st, const void* in, void* out, const int64_t
 int exec_launch_ragged(const Step& st, int prec, const void* in, void* out, const int64_t* offs,
                        int64_t batch, cudaStream_t s, const std::vector<cudaStream_t>& side,
                        const std::vector<cudaEvent_t>& ev) {
-    if (prec == TDH_FP32) return launch_ragged_typed<float>(st, in, out, offs, batch, s, side, ev);
+    if (prec != TDH_FP64) return launch_ragged_typed<float>(st, in, out, offs, batch, s, side, ev);
     return launch_ragged_typed<double>(st, in, out, offs, batch, s, side, ev);
 }
 
 int exec_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
                 cudaStream_t s) {
     if (st.ex.multipass) return mp_launch(st, prec, in, out, batch, adjoint, s);
-    if (prec == TDH_FP32) return launch_typed<float>(st, in, out, batch, adjoint, s);
+    if (prec != TDH_FP64) return launch_typed<float>(st, in, out, batch, adjoint, s);
     return launch_typed<double>(st, in, out, batch, adjoint, s);
 }
 
@@ -597,7 +625,7 @@ int rebuild_config(const ConfigRef& r, int prec, const Geometry& g, cudaStream_t
     const bool nat = r.cls >= 0 && g.C == 1;  // ragged single-CTA classes share u_nat
     const void* su = nat ? r.st->u_nat : nullptr;
     const int64_t ss = nat ? (r.st->n + 1) / 2 : 0;
-    const int rc = prec == TDH_FP32 ? prepare_typed<float>(*r.st, nx, g, su, ss, s)
+    const int rc = prec != TDH_FP64 ? prepare_typed<float>(*r.st, nx, g, su, ss, s)
                                     : prepare_typed<double>(*r.st, nx, g, su, ss, s);
     if (rc != TDH_OK) {
         exec_release(nx);
@@ -809,7 +837,7 @@ int exec_autotune(tdh_plan_s& plan, int64_t batch, cudaStream_t s) {
         set_error("autotune batch must be >= 1");
         return TDH_ERR_INVALID_ARG;
     }
-    if (plan.params.prec == TDH_FP32) return autotune_typed<float>(plan, batch, s);
+    if (plan.params.prec != TDH_FP64) return autotune_typed<float>(plan, batch, s);
     return autotune_typed<double>(plan, batch, s);
 }
 

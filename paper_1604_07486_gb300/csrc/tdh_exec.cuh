@@ -27,6 +27,7 @@
 
 #include "tdh_fft.cuh"
 #include "tdh_internal.cuh"
+#include "tdh_tc.cuh"
 
 namespace tdh {
 
@@ -107,6 +108,30 @@ struct SchedTable<false> {
     static constexpr int size = (int)(sizeof(kSchedF64) / sizeof(Sched));
     static constexpr Sched at(int i) { return kSchedF64[i]; }
 };
+// Split-bfloat16 tensor-core schedules (TDH_BF16X3): the float32 geometries with one CTA per
+// SM's worth of registers, and the two-CTA variants of the 8192-point slices.
+constexpr Sched kSchedTC[] = {
+    {8, 1, 32, 1},   {9, 1, 64, 1},   {10, 1, 64, 1},  {11, 1, 128, 1}, {12, 1, 256, 1},
+    {13, 1, 512, 1}, {14, 1, 512, 1}, {14, 2, 512, 1}, {14, 4, 512, 1}, {14, 8, 512, 1},
+    {13, 2, 256, 2}, {13, 4, 256, 2}, {13, 8, 256, 2}, {9, 2, 64, 1},   {8, 4, 32, 1},
+    {10, 2, 64, 1},  {11, 2, 128, 1}, {12, 2, 256, 2},
+};
+struct SchedTableTC {
+    static constexpr int size = (int)(sizeof(kSchedTC) / sizeof(Sched));
+    static constexpr Sched at(int i) { return kSchedTC[i]; }
+};
+
+// Tensor-core passes: TMEM columns a CTA allocates for local length 2^LOGLC, radix R and NT
+// threads.  A middle pass of LC / R groups runs as tiles of RT = min(NT, 128) groups (one
+// group per TMEM lane); a tile holds its A operand as split-bfloat16 hi and lo rows (R
+// columns each) and its float32 result D (2R columns).
+__host__ __device__ constexpr int tc_rows(int NT) { return NT < 128 ? NT : 128; }
+__host__ __device__ constexpr int tc_cols(int LOGLC, int R, int NT) {
+    const int need = ((1 << LOGLC) / R / tc_rows(NT)) * 4 * R;
+    int c = 32;
+    while (c < need) c *= 2;
+    return c;
+}
 
 template <typename T>
 struct ExecParams {
@@ -141,6 +166,9 @@ struct ExecParams {
     const int* list;
     const int* count;
     int* next;
+    // device status word (TDH_STATUS_* bits, may be null): a tensor-core pass whose MMA wait
+    // ran out of time sets TDH_STATUS_TIMEOUT
+    int* status;
 };
 
 #ifndef TDH_SMEM_PAD
@@ -258,34 +286,184 @@ __device__ __forceinline__ void pass_inv(V* buf, const V* tw) {
     }
 }
 
-template <int I, int LOGLC, int R, int NT, typename V>
-__device__ __forceinline__ void middle_fwd(V* buf, const V* twt) {
-    constexpr PassGeom G{LOGLC, R};
-    if constexpr (I <= G.np() - 2) {
-        pass_fwd<G.rad(I), G.M(I), G.S(I), G.LC(), NT>(buf, twt + G.twoff(I));
-        __syncthreads();
-        middle_fwd<I + 1, LOGLC, R, NT>(buf, twt);
+// ------------------------------------------------------------ split-bfloat16 DFT-GEMM passes
+//
+// A middle pass as a matrix product on the tensor cores (TDH_BF16X3).  Group g (offset o,
+// block b) holds the RAD points x_q = buf[b M + o + q S]; as a row of 2 RAD reals (re, im
+// interleaved) its radix-RAD DFT is one row of A W, W the 2 RAD x 2 RAD real form of the DFT
+// matrix.  Both factors are split, A = Ah + Al and W = Wh + Wl (bfloat16 hi and lo parts), and
+// the three products Ah Wh + Al Wh + Ah Wl accumulate in float32 in tensor memory (the
+// dropped Al Wl is below 2^-17 of the product).  Forward: D = A W, then the twiddles
+// omega_M^{p o} in float32; inverse: the conjugate twiddles first, then the product with the
+// conjugate DFT matrix.  Same values as pass_fwd / pass_inv up to the split's rounding.
+//
+// Per-CTA state: TMEM base address, the four B matrices in shared memory (forward hi, lo,
+// inverse hi, lo; K-major core-matrix layout), the MMA-completion mbarrier and its phase.
+struct TcState {
+    uint32_t tmem;
+    uint32_t bsm;
+    uint32_t mbar;
+    uint32_t phase;
+    int* fail;    // shared: set once a wait ran out (later passes do not wait)
+    int* status;  // global status word or null
+};
+
+// Limit of one wait for the MMAs of a pass (they take microseconds).
+constexpr uint64_t kTcWaitNs = 1000000000ull;
+
+// W (forward: sign +1; inverse: -1) in bfloat16 hi/lo parts, K-major core matrices: element
+// (n, k) at byte (k/8 (N/8) + n/8) 128 + (n%8) 16 + (k%8) 2, N = 2 RAD.
+template <int RAD, int NT>
+__device__ __forceinline__ void tc_build_dft(unsigned char* bsm) {
+    constexpr int N = 2 * RAD;
+    constexpr int BM = N * N * 2;
+    for (int i = threadIdx.x; i < 2 * N * N; i += NT) {
+        const int inv = i / (N * N), e = i % (N * N);
+        const int n = e / N, k = e % N;
+        const int a = n >> 1, b = k >> 1;
+        const int r = (a * b) % RAD;
+        double sn, cs;
+        sincospi(2.0 * (double)r / (double)RAD, &sn, &cs);
+        const double sig = inv ? -1.0 : 1.0;
+        // out_re = c x_re + sig s x_im ; out_im = -sig s x_re + c x_im
+        const double w = ((n & 1) == (k & 1)) ? cs : ((n & 1) == 0 ? sig * sn : -sig * sn);
+        const __nv_bfloat16 hi = __double2bfloat16(w);
+        const __nv_bfloat16 lo = __double2bfloat16(w - (double)__bfloat162float(hi));
+        const int off = ((k >> 3) * (N / 8) + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(bsm + inv * 2 * BM + off) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(bsm + inv * 2 * BM + BM + off) = lo;
     }
 }
 
-template <int I, int LOGLC, int R, int NT, typename V>
-__device__ __forceinline__ void middle_inv(V* buf, const V* twt) {
+template <int RAD, int M, int S, int LC, int NT, bool FWD>
+__device__ __forceinline__ void tc_pass(float2* buf, const float2* tw, TcState& ts) {
+    static_assert(NT % S == 0, "thread count must be a multiple of the pass stride");
+    static_assert(RAD == 8 || RAD == 16, "tensor-core passes are radix 8 or 16");
+    using V = float2;
+    constexpr int G = LC / RAD;            // groups: one TMEM lane (row of A and D) each
+    constexpr int J = G / NT;              // groups per thread
+    constexpr int RT = tc_rows(NT);        // rows per tile
+    constexpr int CT = 4 * RAD;            // TMEM columns per tile: hi, lo (RAD each), D (2 RAD)
+    constexpr int T = G / RT;              // tiles
+    constexpr int N = 2 * RAD;             // MMA N (and K of one operand part)
+    constexpr int NCH = N / 16;            // K = 16 chunks per part
+    constexpr uint32_t KST = (N / 8) * 128;   // bytes between K-adjacent core matrices of W
+    constexpr uint32_t BM = N * N * 2;
+    static_assert(J >= 1 && G % NT == 0 && G % RT == 0, "groups must divide over threads");
+    const int tid = threadIdx.x;
+    const uint32_t lane_base = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
+    V wp[RAD];
+    powers<RAD>(tw[S + tid % S], wp);
+    // 1. split rows into TMEM (inverse: conjugate twiddles first)
+#pragma unroll 1
+    for (int i = 0; i < J; ++i) {
+        const int g = tid + i * NT;
+        const int t = g / RT;
+        const int base = (g / S) * M + (g % S);
+        uint32_t hi[RAD], lo[RAD];
+#pragma unroll
+        for (int q = 0; q < RAD; ++q) {
+            V x = buf[sidx<V>(base + q * S)];
+            if (!FWD && q > 0) x = cmulc(x, wp[q]);
+            tc::split2(x.x, x.y, hi[q], lo[q]);
+        }
+        const uint32_t col = ts.tmem + lane_base + (uint32_t)(t * CT);
+        if constexpr (RAD == 16) {
+            tc::tmem_st16(col, hi);
+            tc::tmem_st16(col + RAD, lo);
+        } else {
+            tc::tmem_st8(col, hi);
+            tc::tmem_st8(col + RAD, lo);
+        }
+    }
+    tc::tmem_wait_st();
+    tc::fence_before_sync();
+    __syncthreads();
+    // 2. one thread issues the three split products of every tile
+    if (tid == 0) {
+        tc::fence_after_sync();
+        constexpr uint32_t idesc = tc::idesc_bf16(128, N);
+        const uint32_t wh = ts.bsm + (FWD ? 0u : 2u * BM), wl = wh + BM;
+#pragma unroll 1
+        for (int t = 0; t < T; ++t) {
+            const uint32_t a = ts.tmem + (uint32_t)(t * CT);
+            const uint32_t d = a + 2 * RAD;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                tc::mma_ts(d, a + 8 * c, tc::smem_desc(wh + c * 2 * KST, KST, 128), idesc,
+                           c > 0 ? 1u : 0u);
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                tc::mma_ts(d, a + RAD + 8 * c, tc::smem_desc(wh + c * 2 * KST, KST, 128), idesc, 1u);
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+                tc::mma_ts(d, a + 8 * c, tc::smem_desc(wl + c * 2 * KST, KST, 128), idesc, 1u);
+        }
+        tc::mma_commit(ts.mbar);
+    }
+    // 3. wait for the products (bounded), read D, twiddle (forward), store
+    if (!*ts.fail && !tc::mbar_wait_bounded(ts.mbar, ts.phase, kTcWaitNs)) {
+        *ts.fail = 1;
+        if (ts.status) atomicOr(ts.status, TDH_STATUS_TIMEOUT);
+    }
+    ts.phase ^= 1u;
+    __syncwarp();
+    tc::fence_after_sync();
+#pragma unroll 1
+    for (int i = 0; i < J; ++i) {
+        const int g = tid + i * NT;
+        const int t = g / RT;
+        const int base = (g / S) * M + (g % S);
+        const uint32_t col = ts.tmem + lane_base + (uint32_t)(t * CT + 2 * RAD);
+        uint32_t dv[N];
+        if constexpr (RAD == 16)
+            tc::tmem_ld32(col, dv);
+        else
+            tc::tmem_ld16(col, dv);
+#pragma unroll
+        for (int p = 0; p < RAD; ++p) {
+            V y = mk<V>(__uint_as_float(dv[2 * p]), __uint_as_float(dv[2 * p + 1]));
+            if (FWD && p > 0) y = cmul(y, wp[p]);
+            buf[sidx<V>(base + p * S)] = y;
+        }
+    }
+    tc::fence_before_sync();
+}
+
+template <int I, int LOGLC, int R, int NT, bool TC, typename V>
+__device__ __forceinline__ void middle_fwd(V* buf, const V* twt, TcState* ts) {
+    constexpr PassGeom G{LOGLC, R};
+    if constexpr (I <= G.np() - 2) {
+        if constexpr (TC)
+            tc_pass<G.rad(I), G.M(I), G.S(I), G.LC(), NT, true>(buf, twt + G.twoff(I), *ts);
+        else
+            pass_fwd<G.rad(I), G.M(I), G.S(I), G.LC(), NT>(buf, twt + G.twoff(I));
+        __syncthreads();
+        middle_fwd<I + 1, LOGLC, R, NT, TC>(buf, twt, ts);
+    }
+}
+
+template <int I, int LOGLC, int R, int NT, bool TC, typename V>
+__device__ __forceinline__ void middle_inv(V* buf, const V* twt, TcState* ts) {
     constexpr PassGeom G{LOGLC, R};
     if constexpr (I >= 1) {
-        pass_inv<G.rad(I), G.M(I), G.S(I), G.LC(), NT>(buf, twt + G.twoff(I));
+        if constexpr (TC)
+            tc_pass<G.rad(I), G.M(I), G.S(I), G.LC(), NT, false>(buf, twt + G.twoff(I), *ts);
+        else
+            pass_inv<G.rad(I), G.M(I), G.S(I), G.LC(), NT>(buf, twt + G.twoff(I));
         __syncthreads();
-        middle_inv<I - 1, LOGLC, R, NT>(buf, twt);
+        middle_inv<I - 1, LOGLC, R, NT, TC>(buf, twt, ts);
     }
 }
 
 // One vector: v = D alpha -> all K rank terms -> beta (the whole of Fig. 1 steps 3-5).
-template <typename T, int LOGLC, int R, int C, int NT>
+template <typename T, int LOGLC, int R, int C, int NT, bool TC>
 __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* in, T* out,
                                                const int64_t n, const int k1,
                                                typename cx<T>::t* buf, typename cx<T>::t* vbuf,
                                                const typename cx<T>::t* twt, T* red,
                                                const int64_t r_begin, const int64_t r_end,
-                                               const bool lead) {
+                                               const bool lead, TcState* ts) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
     constexpr int LC = G.LC();
@@ -364,7 +542,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             }
         }
         __syncthreads();
-        middle_fwd<1, LOGLC, R, NT>(buf, twt);
+        middle_fwd<1, LOGLC, R, NT, TC>(buf, twt, ts);
         // ---- last pass (stride 1), spectrum, first inverse pass
         if constexpr (C == 1) {
 #pragma unroll 1
@@ -488,7 +666,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             }
             __syncthreads();
         }
-        middle_inv<G.np() - 2, LOGLC, R, NT>(buf, twt);
+        middle_inv<G.np() - 2, LOGLC, R, NT, TC>(buf, twt, ts);
         // ---- inverse pass 0: outputs [0, LC/2) only, accumulate u_r o y
 #pragma unroll
         for (int j = 0; j < J0; ++j) {
@@ -580,7 +758,16 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 // Dense batches: cluster blockIdx.x / C converts vector blockIdx.x / C.  Ragged batches
 // (RAGGED): persistent clusters take vectors of one FFT-length class from a work counter.
 // Two kernels so that each inlines the per-vector body once (register pressure).
-template <typename T, int LOGLC, int R, int C, int NT, int MINB, bool RAGGED>
+// Bytes of dynamic shared memory before the tensor-core passes' DFT matrices (FFT buffer,
+// input pairs, twiddles), rounded up to 128, and the matrices' size (four 2R x 2R bfloat16).
+template <typename V>
+__host__ __device__ constexpr size_t exec_smem_base(int LOGLC, int R) {
+    return ((size_t)(padded_len<V>(1 << LOGLC) + (1 << LOGLC) / 2 +
+                     PassGeom{LOGLC, R}.twp_len()) * sizeof(V) + 127) / 128 * 128;
+}
+__host__ __device__ constexpr size_t tc_dft_bytes(int R) { return (size_t)4 * (2 * R) * (2 * R) * 2; }
+
+template <typename T, int LOGLC, int R, int C, int NT, int MINB, bool RAGGED, bool TC>
 __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
@@ -590,8 +777,9 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
     constexpr int TWP = G.twp_len();
     static_assert(G.np() >= 2, "local FFT needs at least two passes");
     static_assert(J0 >= 1 && S0 % NT == 0, "pass-0 groups must divide over threads");
+    static_assert(!TC || std::is_same<T, float>::value, "tensor-core passes are float32");
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     V* buf = reinterpret_cast<V*>(smem_raw);  // [LC] FFT buffer, padded rows
     V* vbuf = buf + padded_len<V>(LC);        // [LC/2] scaled input pairs
     V* twt = vbuf + LC / 2;                   // [TWP] middle-pass twiddles
@@ -601,6 +789,36 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
     int k1 = 0;
     if constexpr (C > 1) k1 = (int)cg::this_cluster().block_rank();
     for (int i = tid; i < TWP; i += NT) twt[i] = P.twp[i];
+
+    // tensor-core passes: DFT matrices in shared memory, TMEM for A and D, one mbarrier
+    constexpr int TCOLS = tc_cols(LOGLC, R, NT);
+    __shared__ uint32_t tc_slot;
+    __shared__ __align__(8) uint64_t tc_mbar;
+    __shared__ int tc_fail;
+    TcState tcs{};
+    if constexpr (TC) {
+        unsigned char* bsm = smem_raw + exec_smem_base<V>(LOGLC, R);
+        tc_build_dft<R, NT>(bsm);
+        tc::fence_proxy_async_smem();
+        if (tid < 32) {
+            tc::tmem_alloc(tc::smem_u32(&tc_slot), TCOLS);
+            tc::tmem_relinquish();
+        }
+        if (tid == 0) {
+            tc::mbar_init(tc::smem_u32(&tc_mbar), 1);
+            tc::mbar_fence_init();
+            tc_fail = 0;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tcs.tmem = tc_slot;
+        tcs.bsm = tc::smem_u32(bsm);
+        tcs.mbar = tc::smem_u32(&tc_mbar);
+        tcs.phase = 0;
+        tcs.fail = &tc_fail;
+        tcs.status = P.status;
+    }
     if constexpr (!RAGGED) {
         const int64_t G = gridDim.x / C;
         const int64_t cid = blockIdx.x / C;
@@ -614,8 +832,9 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
             const int64_t r1 = r0 + u1 - u < Ku ? r0 + u1 - u : Ku;
             T* outp = (r0 == 0 && r1 == Ku) ? P.out + vec * P.n
                                             : P.partial + (2 * cid + (r0 == 0 ? 1 : 0)) * P.n;
-            convert_vector<T, LOGLC, R, C, NT>(P, P.in + vec * P.n, outp, P.n, k1, buf, vbuf, twt,
-                                               red, r0, r1 < P.K ? r1 : P.K, r0 == 0);
+            convert_vector<T, LOGLC, R, C, NT, TC>(P, P.in + vec * P.n, outp, P.n, k1, buf, vbuf,
+                                                   twt, red, r0, r1 < P.K ? r1 : P.K, r0 == 0,
+                                                   &tcs);
             u += r1 - r0;
         }
     } else {
@@ -636,10 +855,18 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
             const int64_t vec = P.list[sidx];
             const int64_t off = P.offs[vec];
             const int64_t n = P.offs[vec + 1] - off;
-            convert_vector<T, LOGLC, R, C, NT>(P, P.in + off, P.out + off, n, k1, buf, vbuf, twt,
-                                               red, 0, P.K, true);
+            convert_vector<T, LOGLC, R, C, NT, TC>(P, P.in + off, P.out + off, n, k1, buf, vbuf,
+                                                   twt, red, 0, P.K, true, &tcs);
         }
         if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its slot is read
+    }
+    if constexpr (TC) {  // every tensor-memory access of the CTA is complete: free it
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid < 32) {
+            tc::fence_after_sync();
+            tc::tmem_dealloc(tcs.tmem, TCOLS);
+        }
     }
 }
 
@@ -661,13 +888,32 @@ __global__ void k_balance_fixup(const T* __restrict__ partial, T* __restrict__ o
     out[v * n + k] = acc;
 }
 
-template <typename T, int LOGLC, int R, int C, int NT, int MINB, bool RAGGED>
+// Dynamic shared memory of a launch.  Tensor-core kernels also hold the DFT matrices, and at
+// least enough shared memory that the CTAs resident on one SM can never ask for more than the
+// SM's 512 TMEM columns together (tcgen05.alloc would otherwise wait for another CTA's columns,
+// and CTAs of a cluster waiting on each other could then never proceed): with at most
+// k = 512 / TCOLS CTAs allowed, each takes more than 1/(k+1) of the SM's 228 KB.
+template <typename V, int LOGLC, int R, int NT, bool TC>
+constexpr size_t exec_smem() {
+    if constexpr (!TC) {
+        return (size_t)(padded_len<V>(1 << LOGLC) + (1 << LOGLC) / 2 +
+                        PassGeom{LOGLC, R}.twp_len()) * sizeof(V);
+    } else {
+        const size_t need = exec_smem_base<V>(LOGLC, R) + tc_dft_bytes(R);
+        const size_t k = (size_t)(512 / tc_cols(LOGLC, R, NT));
+        const size_t floor_bytes = (size_t)233472 / (k + 1) - 1024 + 128;
+        return need > floor_bytes ? need : floor_bytes;
+    }
+}
+
+template <typename T, int LOGLC, int R, int C, int NT, int MINB, bool RAGGED, bool TC>
 int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
     using V = typename cx<T>::t;
     constexpr PassGeom G{LOGLC, R};
-    constexpr size_t smem = (size_t)(padded_len<V>(G.LC()) + G.LC() / 2 + G.twp_len()) * sizeof(V);
+    constexpr size_t smem = exec_smem<V, LOGLC, R, NT, TC>();
     static_assert(smem <= 232448, "shared memory budget");
-    auto kern = exec_kernel<T, LOGLC, R, C, NT, MINB, RAGGED>;
+    static_assert(!TC || tc_cols(LOGLC, R, NT) <= 512, "tensor memory budget");
+    auto kern = exec_kernel<T, LOGLC, R, C, NT, MINB, RAGGED, TC>;
     static PerDevice attr_once;
     const cudaError_t attr_err = per_device(attr_once, [&](int*) {
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -752,12 +998,29 @@ int dispatch_geom(const Geometry& g, const ExecParams<T>& P, int64_t batch, cuda
     if constexpr (I < SchedTable<f32>::size) {
         constexpr Sched e = SchedTable<f32>::at(I);
         if (g.logLC == e.logLC && g.C == e.C && g.NT == e.NT && g.MINB == e.MINB)
-            return launch_inst<T, e.logLC, radix_for(f32, e.logLC), e.C, e.NT, e.MINB, RAGGED>(
-                P, batch, s);
+            return launch_inst<T, e.logLC, radix_for(f32, e.logLC), e.C, e.NT, e.MINB, RAGGED,
+                               false>(P, batch, s);
         return dispatch_geom<T, RAGGED, I + 1>(g, P, batch, s);
     } else {
         set_error("no %s kernel for local length 2^%d, cluster %d, %d threads, %d CTAs per SM",
                   f32 ? "float32" : "float64", g.logLC, g.C, g.NT, g.MINB);
+        return TDH_ERR_UNSUPPORTED;
+    }
+}
+
+// The same over the split-bfloat16 tensor-core instantiations.
+template <bool RAGGED, int I = 0>
+int dispatch_geom_tc(const Geometry& g, const ExecParams<float>& P, int64_t batch,
+                     cudaStream_t s) {
+    if constexpr (I < SchedTableTC::size) {
+        constexpr Sched e = SchedTableTC::at(I);
+        if (g.logLC == e.logLC && g.C == e.C && g.NT == e.NT && g.MINB == e.MINB)
+            return launch_inst<float, e.logLC, radix_for(true, e.logLC), e.C, e.NT, e.MINB,
+                               RAGGED, true>(P, batch, s);
+        return dispatch_geom_tc<RAGGED, I + 1>(g, P, batch, s);
+    } else {
+        set_error("no split-bfloat16 kernel for local length 2^%d, cluster %d, %d threads, "
+                  "%d CTAs per SM", g.logLC, g.C, g.NT, g.MINB);
         return TDH_ERR_UNSUPPORTED;
     }
 }
@@ -767,5 +1030,8 @@ int dispatch_dense(const Geometry& g, const ExecParams<float>& P, int64_t batch,
 int dispatch_dense(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s);
 int dispatch_ragged(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s);
 int dispatch_ragged(const Geometry& g, const ExecParams<double>& P, int64_t batch, cudaStream_t s);
+// Defined in tdh_dense_tc.cu and tdh_ragged_tc.cu (split-bfloat16 tensor-core passes).
+int dispatch_dense_tc(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s);
+int dispatch_ragged_tc(const Geometry& g, const ExecParams<float>& P, int64_t batch, cudaStream_t s);
 
 }  // namespace tdh

@@ -109,6 +109,7 @@ struct Geometry {
     int R;      // radix of the local passes
     int NT;     // threads per CTA
     int MINB;   // CTAs per SM the kernel's registers are capped for (launch bounds)
+    int tc;     // 1: middle passes as split-bfloat16 tensor-core DFT products (TDH_BF16X3)
 };
 
 // Device data of one execute configuration.
@@ -141,6 +142,7 @@ struct Step {
     int full = 0;          // Toeplitz part without parity structure (Jacobi): rank-pair packing
     int sign_in = 0;       // (-1)^k on the input (reflection step of a Jacobi chain)
     int sign_out = 0;      // (-1)^k on the output
+    int* status = nullptr;  // the plan's device status word (TDH_STATUS_* bits)
     // Case-1 step (Sec. 5.2, 5.3): sp_M > 0 sparse factors instead of T o H
     int sp_M = 0;
     int sp_family = 0;     // SP_ULTRA (offset 2), SP_JACOBI (offset 1), SP_IDENTITY
@@ -180,6 +182,7 @@ struct tdh_plan_s {
     double tol = 0;
     int device = 0;
     std::vector<tdh::Step> steps;
+    int* status = nullptr;  // device: TDH_STATUS_* bits recorded by kernels (tdh_plan_status)
     std::vector<cudaStream_t> side;  // ragged batches: one stream per length class
     std::vector<cudaEvent_t> ev;     // fork/join events (ev[0] fork, ev[1+i] joins)
     // host-buffer execution: copy-in and copy-out streams and their events

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_fwd(const MPParams<T
         }
     }
     __syncthreads();
-    middle_fwd<1, LOGLC, R, NT>(buf, twt);
+    middle_fwd<1, LOGLC, R, NT, false>(buf, twt, (TcState*)nullptr);
 #pragma unroll 1
     for (int g = tid; g < LC / RL; g += NT) {
         V x[RL];
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T
         for (int q = 0; q < RL; ++q) buf[sidx<V>(g * RL + q)] = x[q];
     }
     __syncthreads();
-    middle_inv<G.np() - 2, LOGLC, R, NT>(buf, twt);
+    middle_inv<G.np() - 2, LOGLC, R, NT, false>(buf, twt, (TcState*)nullptr);
 #pragma unroll
     for (int j = 0; j < J0; ++j) {
         const int o = tid + j * NT;
@@ -632,7 +632,7 @@ int mp_launch(const Step& st, int prec, const void* in, void* out, int64_t batch
         return TDH_ERR_UNSUPPORTED;
     }
     // slices one below the shared-memory cap run two CTAs per SM; longer FFTs keep full slices
-    if (prec == TDH_FP32)
+    if (prec != TDH_FP64)
         return st.ex.g.logLC == 13 ? run_typed<float, 13, 16, 256>(st, in, out, batch, adjoint, s)
                                    : run_typed<float, 14, 16, 512>(st, in, out, batch, adjoint, s);
     return st.ex.g.logLC == 12 ? run_typed<double, 12, 8, 256>(st, in, out, batch, adjoint, s)

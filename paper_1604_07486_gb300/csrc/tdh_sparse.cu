@@ -654,10 +654,10 @@ int sparse_prepare(Step& st, int prec, cudaStream_t s) {
     F.ld = (st.n + 2 + 3) / 4 * 4;  // float4 rows stay 16-byte aligned
     st.sp_ld = F.ld;
     const int rows = st.sp_inverse ? kInvRows : 2;
-    const size_t esz = prec == TDH_FP32 ? 4 : 8;
+    const size_t esz = prec != TDH_FP64 ? 4 : 8;
     TDH_TRY(dev_alloc(&st.sp_tab, esz * (size_t)F.ld * rows * st.sp_M));
     const unsigned blocks = blocks_for(F.ld * F.M);
-    if (prec == TDH_FP32)
+    if (prec != TDH_FP64)
         k_sparse_tables<float><<<blocks, kThreads, 0, s>>>(F, st.scale_out, st.scale_in,
                                                            static_cast<float*>(st.sp_tab));
     else
@@ -669,7 +669,7 @@ int sparse_prepare(Step& st, int prec, cudaStream_t s) {
 
 int sparse_launch(const Step& st, int prec, const void* in, void* out, int64_t batch, int adjoint,
                   cudaStream_t s) {
-    if (prec == TDH_FP32) return launch_typed<float>(st, in, out, batch, adjoint, s);
+    if (prec != TDH_FP64) return launch_typed<float>(st, in, out, batch, adjoint, s);
     return launch_typed<double>(st, in, out, batch, adjoint, s);
 }
 
