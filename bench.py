@@ -306,6 +306,93 @@ def precision_comparison(tdh, args, flush, stream, world, rank, n=1 << 20, batch
     return out
 
 
+def dense_arm_bf16x3(tdh, args, alpha, flush, stream, world, rank, rows):
+    """Both directions at n = 2^16, batch 256 with the split-bfloat16 tensor-core DFT passes
+    (TDH_BF16X3), tuned, timed like the float32 line; errors against the oracle."""
+    import torch
+    plans = {k: tdh.Plan(k, N, prec="bf16x3") for k in KINDS}
+    sched = {k: tune(plans[k], BATCH, args)[1] for k in KINDS}
+    x = torch.tensor(alpha, dtype=torch.float32, device="cuda")
+    y = {k: torch.empty_like(x) for k in KINDS}
+    for _ in range(args.warmup):
+        for k in KINDS:
+            plans[k].execute(x, out=y[k])
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in KINDS:
+            plans[k].execute(x, out=y[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    value = world * len(KINDS) * BATCH * N * args.steps / (sum(ms) / 1e3)
+    err = {k: oracle_error(alpha, y[k].double().cpu().numpy(), k, [0, BATCH - 1], rows)
+           for k in KINDS} if rank == 0 else None
+    return {"value": value, "unit": "coeffs/s", "ms_per_step": sum(ms) / args.steps,
+            "K": {k: plans[k].K for k in KINDS}, "schedule": sched, "error_vs_oracle": err,
+            "tolerance": 1e-5, "status": {k: sorted(plans[k].status()) for k in KINDS}}
+
+
+def ragged_arm_bf16x3(tdh, args, xv, offs, lengths, flops, fp32_peak, apeaks, flush, stream,
+                      world, dist, rank):
+    """Config 3's second arm: the same ragged batch with the split-bfloat16 tensor-core DFT
+    passes (TDH_BF16X3), tuned, replayed from one CUDA graph, timed like the float32 arm."""
+    import numpy as np
+    import torch
+    import oracle
+    plan = tdh.Plan("leg2cheb", int(lengths.max()), prec="bf16x3", ragged=True)
+    tune_ms, sched = tune(plan, len(lengths), args)
+    xt = torch.tensor(xv, dtype=torch.float32, device="cuda")
+    ot = torch.tensor(offs, dtype=torch.int64, device="cuda")
+    yt = torch.empty_like(xt)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        plan.execute_ragged(xt, ot, out=yt)
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.execute_ragged(xt, ot, out=yt)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    coeffs = int(offs[-1])
+    value, total_ms = job_throughput(sum(ms), coeffs, args.steps, world, dist)
+    achieved = flops * args.steps / (total_ms / 1e3) / 1e12
+    err = None
+    if rank == 0:
+        yn = yt.double().cpu().numpy()
+        errs = []
+        for i in [int(np.argmax(lengths)), 0, 1000, 4095]:
+            a, b = int(offs[i]), int(offs[i + 1])
+            rows = np.r_[np.arange(32), b - a - 32 + np.arange(32)]
+            ref = oracle.matvec(oracle.LEG2CHEB, None, xv[a:b], rows=rows)
+            errs.append(np.abs(yn[a:b][rows] - ref).max() / np.abs(xv[a:b]).sum())
+        err = float(max(errs))
+    return {"value": value, "unit": "coeffs/s", "ms_per_step": total_ms / args.steps,
+            "K": plan.K, "plan": {"tol": plan.tol, "target": True}, "schedule": sched,
+            "autotune_ms": tune_ms, "error_vs_oracle": err, "tolerance": 1e-5,
+            "status": sorted(plan.status()),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "peak_note": "same algorithmic flops as the float32 arm, against the "
+                                      "FP32 FFMA " + apeaks["note"]},
+            "note": "radix-16/8 middle FFT passes as split-bfloat16 tcgen05 DFT products; "
+                    "other passes float32"}
+
+
 def workloads_coefficients(n, batch, seed):
     import workloads
     return workloads.coefficients(n, batch, decay=DECAY, seed=seed)
@@ -319,6 +406,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-bf16x3", action="store_true",
+                    help="skip the split-bfloat16 tensor-core arm")
     ap.add_argument("--no-big", action="store_true",
                     help="skip the float32-vs-float64 comparison at n = 2^20")
     ap.add_argument("--no-autotune", action="store_true",
@@ -418,9 +507,9 @@ def main():
 
     # accuracy of the timed outputs against the oracle (sampled rows)
     err = {}
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.r_[np.arange(16), N - 1 - np.arange(16), rng.integers(0, N, 32)])
     if rank == 0:
-        rng = np.random.default_rng(3)
-        rows = np.unique(np.r_[np.arange(16), N - 1 - np.arange(16), rng.integers(0, N, 32)])
         for k in KINDS:
             err[k] = oracle_error(alpha, ys[k].double().cpu().numpy(), k, [0, BATCH - 1], rows)
 
@@ -456,6 +545,11 @@ def main():
                              "frac": flops64 / (ms64 / reps / 1e3) / 1e12 / apeaks["fp64"],
                              "peak_note": "FP64 DFMA " + apeaks["note"]}}
         del plans64, x64, y64
+
+    # split-bfloat16 tensor-core arm on the same workload (TDH_BF16X3)
+    bf = None
+    if not args.no_bf16x3:
+        bf = dense_arm_bf16x3(tdh, args, alpha, flush, stream, world, rank, rows)
 
     # the benchmark spec's precision claim across n = 2^16 .. 2^20: float32 against float64 at
     # n = 2^20 (multi-pass FFTs), Legendre -> Chebyshev, batch 16
@@ -507,6 +601,7 @@ def main():
             "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
                     "note": "8 algorithmic bytes per coefficient (fp32 in + out); of measured"},
             "fp64": fp64,
+            "bf16x3": bf,
             "fp32_vs_fp64_n2p20": big,
             "e2e": {"value": e2e_value, "unit": "coeffs/s", "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
@@ -717,6 +812,9 @@ def run_extra(args, rank, world, local):
                                      "frac": dn_gbs / hbm_peak, "traffic": None, "ms": statistics.mean(dn_ms),
                                      "note": "ultraspherical 1.25 -> 0.25 (three scan kernels), 8 algorithmic "
                                              "bytes per coefficient; of measured; not part of value"}
+    if w == "c3":
+        extra["bf16x3"] = ragged_arm_bf16x3(tdh, args, xv, offs, lengths, flops, fp32_peak,
+                                            apeaks, flush, stream, world, dist, rank)
     err = check() if (check and rank == 0) else None
     # end to end through the public API with pinned host buffers
     for _ in range(2):

@@ -226,8 +226,9 @@ int tdh_plan_schedule_count(tdh_plan_t plan, int* count);
  * tdh_schedules -- host only (no device call): the compiled schedules for an FFT of 2^logL
  * points in precision prec, the default first (ragged != 0: only those usable by ragged
  * batches, i.e. within one cluster).  out (host, 6 ints per schedule: log2 LC, C, R, NT,
- * MINB, 1 if multi-pass) receives at most cap schedules; *count the number there are (0 when
- * no kernel covers that length).  Errors: INVALID_ARG.
+ * MINB, and 0 within one cluster, 1 multi-pass, 2 multi-pass whose cross stage moves its
+ * blocks by bulk tensor copies (TMA)) receives at most cap schedules; *count the number there
+ * are (0 when no kernel covers that length).  Errors: INVALID_ARG.
  */
 int tdh_schedules(int prec, int logL, int ragged, int* out, int cap, int* count);
 int tdh_plan_schedule_info(tdh_plan_t plan, int config, int* info);
@@ -292,6 +293,17 @@ int tdh_measure_fma_rate(int prec, double* tflops, void* stream);
  * allocation fails; later ones proceed normally.  Errors: INVALID_ARG (k < 0).
  */
 int tdh_test_fail_alloc(int64_t k);
+
+/*
+ * tdh_test_tc_stall -- failure injection for tests (the paper has no counterpart): while on
+ * (on != 0), executes enqueued from then on with TDH_BF16X3 plans issue none of their
+ * tensor-core products, so the first bounded wait of every CTA runs out after about one
+ * second; the kernels then skip their remaining waits, finish, free their tensor memory and
+ * record TDH_STATUS_TIMEOUT (tdh_plan_status).  Their outputs are not valid.  The setting is
+ * process-wide and read when an execute is enqueued (a captured CUDA graph keeps the value it
+ * was captured with).  Returns TDH_OK.
+ */
+int tdh_test_tc_stall(int on);
 
 /*
  * tdh_symbols -- step a1 on its own: the split A = D1 (T o H) D2 of `kind` for n

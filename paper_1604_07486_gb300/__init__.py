@@ -25,7 +25,7 @@ EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "t
            "tdh_plan_execute_ragged", "tdh_launch_count", "tdh_plan_execute_host",
            "tdh_plan_schedule_count", "tdh_plan_schedule_info", "tdh_plan_set_schedule",
            "tdh_plan_autotune", "tdh_schedules", "tdh_alloc_stats", "tdh_test_fail_alloc",
-           "tdh_measure_fma_rate", "tdh_plan_status")
+           "tdh_measure_fma_rate", "tdh_plan_status", "tdh_test_tc_stall")
 FLAG_RAGGED = 1
 FLAG_TARGET = 2
 
@@ -75,6 +75,7 @@ def lib():
         L.tdh_test_fail_alloc.argtypes = [i64]
         L.tdh_measure_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(dbl), vp]
         L.tdh_plan_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
+        L.tdh_test_tc_stall.argtypes = [ctypes.c_int]
         L.tdh_plan_execute_host.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
         L.tdh_plan_schedule_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.tdh_plan_schedule_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
@@ -304,3 +305,9 @@ def measure_fma_rate(prec, stream=None):
     v = ctypes.c_double()
     _check(lib().tdh_measure_fma_rate(prec, ctypes.byref(v), _stream(stream)))
     return float(v.value)
+
+
+def inject_tc_stall(on):
+    """While on, split-bfloat16 executes issue no tensor-core products, so their bounded waits
+    run out and TIMEOUT is recorded (tdh_test_tc_stall; outputs invalid)."""
+    _check(lib().tdh_test_tc_stall(1 if on else 0))

@@ -129,6 +129,12 @@ void alloc_stats(int64_t* out) {
 
 void fail_alloc_after(int64_t k) { g_fail_countdown.store(k > 0 ? k : 0); }
 
+namespace {
+std::atomic<int> g_tc_stall{0};
+}
+int tc_stall_enabled() { return g_tc_stall.load(); }
+void set_tc_stall(int on) { g_tc_stall.store(on ? 1 : 0); }
+
 int sm_count() {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -154,6 +160,9 @@ void release_step(Step& st) {
     dev_free(st.d1x);
     dev_free(st.d2x);
     dev_free(st.row0);
+    dev_free(st.pair_idx);
+    dev_free(st.pair_s);
+    dev_free(st.pair_c);
     exec_release(st.ex);
     st = Step{};
 }
@@ -506,6 +515,12 @@ int tdh_alloc_stats(int64_t* stats) {
         return TDH_ERR_INVALID_ARG;
     }
     tdh::alloc_stats(stats);
+    return TDH_OK;
+}
+
+int tdh_test_tc_stall(int on) {
+    tdh::clear_error();
+    tdh::set_tc_stall(on);
     return TDH_OK;
 }
 

@@ -1,5 +1,6 @@
 // Host side of the execute path: per-plan tables (step a3 and the kernel's twiddles and
 // factor layout) and the launch dispatch over the kernel instantiations.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -24,6 +25,7 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
     g->prec = prec;
     g->logL = logL;
     g->tc = 0;
+    g->tma = 0;
     const int cap = (prec != TDH_FP64) ? 14 : 13;  // largest local FFT held in shared memory
     if (logL <= cap) {
         g->logLC = logL;
@@ -48,7 +50,8 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
 }
 
 bool same_schedule(const Geometry& a, const Geometry& b) {
-    return a.logLC == b.logLC && a.C == b.C && a.NT == b.NT && a.MINB == b.MINB && a.tc == b.tc;
+    return a.logLC == b.logLC && a.C == b.C && a.NT == b.NT && a.MINB == b.MINB && a.tc == b.tc &&
+           a.tma == b.tma;
 }
 
 // Every schedule with a compiled kernel for 2^logL points, the default first: the cluster
@@ -59,7 +62,7 @@ std::vector<Geometry> schedule_candidates(int prec, int logL, bool ragged) {
     Geometry d{};
     if (!choose_geometry(prec, logL, &d)) return out;
     out.push_back(d);
-    auto add = [&](int logLC, int C, int NT, int MINB) {
+    auto add = [&](int logLC, int C, int NT, int MINB, int tma = 0) {
         Geometry g = d;
         g.logLC = logLC;
         g.C = C;
@@ -67,6 +70,7 @@ std::vector<Geometry> schedule_candidates(int prec, int logL, bool ragged) {
         g.NT = NT;
         g.MINB = MINB;
         g.tc = (prec == TDH_BF16X3 && C <= 8) ? 1 : 0;
+        g.tma = tma;
         for (const Geometry& o : out)
             if (same_schedule(o, g)) return;
         out.push_back(g);
@@ -88,6 +92,13 @@ std::vector<Geometry> schedule_candidates(int prec, int logL, bool ragged) {
             int NT, MINB;
             mp_threads(prec, lc, &NT, &MINB);
             add(lc, 1 << (logL - lc), NT, MINB);
+        }
+        // the same multi-pass kernels with the cross stage's block moved by TMA copies
+        for (int lc = cap; lc >= cap - 1; --lc) {
+            if (logL - lc < 4 || logL - lc > 8) continue;  // 16 ... 256 slices
+            int NT, MINB;
+            mp_threads(prec, lc, &NT, &MINB);
+            add(lc, 1 << (logL - lc), NT, MINB, 1);
         }
     }
     if (ragged) {
@@ -204,10 +215,13 @@ __global__ void k_u_gather(const double* __restrict__ u, int64_t n, int64_t K, i
     out[i] = v;
 }
 
-// rank-pair packing: out[rp][k1][k2] = (u[2rp][a], u[2rp+1][a]), a = k1 + C k2
+// rank-pair packing: out[rp][k1][k2] = (u[i0][a], s_rp u[i1][a]), a = k1 + C k2, with
+// (i0, i1) = (idx[2rp], idx[2rp+1]) and s_rp = scale[rp] (the step's pairing)
 template <typename T>
 __global__ void k_u_gather_pairs(const double* __restrict__ u, int64_t n, int64_t K, int C,
-                                 int half, typename cx<T>::t* __restrict__ out) {
+                                 int half, const int* __restrict__ idx,
+                                 const double* __restrict__ scale,
+                                 typename cx<T>::t* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int64_t KP = (K + 1) / 2;
     const int64_t total = KP * C * (int64_t)half;
@@ -216,8 +230,8 @@ __global__ void k_u_gather_pairs(const double* __restrict__ u, int64_t n, int64_
     const int64_t k1 = (i / half) % C;
     const int64_t rp = i / ((int64_t)half * C);
     const int64_t a = k1 + (int64_t)C * k2;
-    T x0 = (a < n) ? (T)u[(2 * rp) * n + a] : T(0);
-    T x1 = (a < n && 2 * rp + 1 < K) ? (T)u[(2 * rp + 1) * n + a] : T(0);
+    T x0 = (a < n) ? (T)u[(int64_t)idx[2 * rp] * n + a] : T(0);
+    T x1 = (a < n && 2 * rp + 1 < K) ? (T)(scale[rp] * u[(int64_t)idx[2 * rp + 1] * n + a]) : T(0);
     typename cx<T>::t v;
     v.x = x0;
     v.y = x1;
@@ -320,7 +334,8 @@ int prepare_typed(Step& st, ExecData& ex, const Geometry& g, const void* shared_
                 st.u64, st.n, st.K, C, LC / 2, (V*)ex.u);
         if (st.K > 0 && st.full && !shared_u)
             k_u_gather_pairs<T><<<blocks_for((st.K + 1) / 2 * C * (int64_t)(LC / 2)), kThreads, 0,
-                                  s>>>(st.u64, st.n, st.K, C, LC / 2, (V*)ex.u);
+                                  s>>>(st.u64, st.n, st.K, C, LC / 2, st.pair_idx, st.pair_s,
+                                       (V*)ex.u);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
@@ -337,6 +352,71 @@ out:
     else
         dev_free(perm_d);
     return rc;
+}
+
+// max_k |u_r[k] d2[k]| for rank term r = blockIdx.x (the size of term r's FFT input per unit
+// of ||alpha||_inf)
+__global__ void __launch_bounds__(kThreads) k_factor_size(const double* __restrict__ u,
+                                                          const double* __restrict__ d2, int64_t n,
+                                                          double* __restrict__ out) {
+    __shared__ double red[kThreads];
+    const double* ur = u + (int64_t)blockIdx.x * n;
+    double m = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += kThreads) m = fmax(m, fabs(ur[k] * d2[k]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int h = kThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// Rank-pair packing puts two rank terms in the real and imaginary parts of one complex FFT,
+// whose rounding is relative to the larger of the two: a term much smaller than its partner
+// would lose its accuracy.  The terms are sorted by size (max_k |u_r[k] D2_k|), paired with
+// their neighbour, and the smaller one is scaled up to its partner's size on the way in
+// (scale s <= 1e6) and back down by 1 / s^2 on the way out (the same table serves both).
+template <typename T>
+int prepare_pairs(Step& st, cudaStream_t s) {
+    const int64_t K = st.K, KP = (K + 1) / 2;
+    std::vector<double> size(K);
+    double* dsize = nullptr;
+    TDH_TRY(dev_alloc_t(&dsize, (size_t)K));
+    k_factor_size<<<(unsigned)K, kThreads, 0, s>>>(st.u64, st.d2, st.n, dsize);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(size.data(), dsize, sizeof(double) * K, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(dsize);
+    if (e != cudaSuccess) {
+        set_error("rank pairing: %s", cudaGetErrorString(e));
+        return TDH_ERR_CUDA;
+    }
+    std::vector<int> idx(K);
+    for (int64_t r = 0; r < K; ++r) idx[r] = (int)r;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return size[a] > size[b]; });
+    std::vector<double> sc(KP, 1.0);
+    std::vector<T> cc(KP, T(1));
+    for (int64_t p = 0; p < KP; ++p) {
+        if (2 * p + 1 >= K) {
+            cc[p] = T(0);
+            continue;
+        }
+        const double big = size[idx[2 * p]], small = size[idx[2 * p + 1]];
+        double f = (small > 0.0 && big > small) ? big / small : 1.0;
+        f = std::min(f, 1e6);
+        sc[p] = f;
+        cc[p] = (T)(1.0 / (f * f));
+    }
+    TDH_TRY(dev_alloc_t(&st.pair_idx, (size_t)K));
+    TDH_TRY(dev_alloc_t(&st.pair_s, (size_t)KP));
+    TDH_TRY(dev_alloc(&st.pair_c, sizeof(T) * (size_t)KP));
+    TDH_CUDA(cudaMemcpyAsync(st.pair_idx, idx.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+    TDH_CUDA(cudaMemcpyAsync(st.pair_s, sc.data(), sizeof(double) * KP, cudaMemcpyHostToDevice, s));
+    TDH_CUDA(cudaMemcpyAsync(st.pair_c, cc.data(), sizeof(T) * KP, cudaMemcpyHostToDevice, s));
+    TDH_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    return TDH_OK;
 }
 
 template <typename T>
@@ -401,6 +481,8 @@ int launch_typed(const Step& st, const void* in, void* out, int64_t batch, int a
     P.batch = batch;
     P.partial = nullptr;
     P.status = st.status;
+    P.tc_stall = tc_stall_enabled();
+    P.pair_c = static_cast<const T*>(st.pair_c);
     return dispatch<T>(ex.g, P, batch, s);
 }
 
@@ -418,9 +500,11 @@ int exec_prepare(Step& st, int prec, cudaStream_t s) {
     }
     if (prec != TDH_FP64) {
         TDH_TRY(prepare_diagonals<float>(st, s));
+        if (st.full && st.K > 0) TDH_TRY(prepare_pairs<float>(st, s));
         return prepare_typed<float>(st, ex, ex.g, nullptr, 0, s);
     }
     TDH_TRY(prepare_diagonals<double>(st, s));
+    if (st.full && st.K > 0) TDH_TRY(prepare_pairs<double>(st, s));
     return prepare_typed<double>(st, ex, ex.g, nullptr, 0, s);
 }
 
@@ -530,6 +614,8 @@ ExecParams<T> ragged_params(const Step& st, const ExecData& ex, const void* in, 
     P.count = count;
     P.next = next;
     P.status = st.status;
+    P.tc_stall = tc_stall_enabled();
+    P.pair_c = nullptr;  // ragged plans are parity-packed
     return P;
 }
 
@@ -790,7 +876,8 @@ int exec_schedules(int prec, int logL, int ragged, int* out, int cap, int* count
     const std::vector<Geometry> c = schedule_candidates(prec, logL, ragged != 0);
     *count = (int)c.size();
     for (int i = 0; i < (int)c.size() && i < cap; ++i) {
-        const int v[6] = {c[i].logLC, c[i].C, c[i].R, c[i].NT, c[i].MINB, c[i].C > 8 ? 1 : 0};
+        const int v[6] = {c[i].logLC, c[i].C, c[i].R, c[i].NT, c[i].MINB,
+                          c[i].C > 8 ? (c[i].tma ? 2 : 1) : 0};
         for (int k = 0; k < 6; ++k) out[6 * i + k] = v[k];
     }
     return TDH_OK;

@@ -169,6 +169,11 @@ struct ExecParams {
     // device status word (TDH_STATUS_* bits, may be null): a tensor-core pass whose MMA wait
     // ran out of time sets TDH_STATUS_TIMEOUT
     int* status;
+    // test hook (tdh_test_tc_stall): tensor-core passes issue no products, so their bounded
+    // waits run out
+    int tc_stall;
+    // rank-pair packing: output factor of each pair's second term (1 / its input scale^2)
+    const T* pair_c;
 };
 
 #ifndef TDH_SMEM_PAD
@@ -298,7 +303,8 @@ __device__ __forceinline__ void pass_inv(V* buf, const V* tw) {
 // conjugate DFT matrix.  Same values as pass_fwd / pass_inv up to the split's rounding.
 //
 // Per-CTA state: TMEM base address, the four B matrices in shared memory (forward hi, lo,
-// inverse hi, lo; K-major core-matrix layout), the MMA-completion mbarrier and its phase.
+// inverse hi, lo; K-major core-matrix layout), the MMA-completion mbarriers (one per
+// warpgroup and tile) and their common phase.
 struct TcState {
     uint32_t tmem;
     uint32_t bsm;
@@ -306,6 +312,7 @@ struct TcState {
     uint32_t phase;
     int* fail;    // shared: set once a wait ran out (later passes do not wait)
     int* status;  // global status word or null
+    int stall;    // test hook: issue no products (every wait runs out)
 };
 
 // Limit of one wait for the MMAs of a pass (they take microseconds).
@@ -335,57 +342,69 @@ __device__ __forceinline__ void tc_build_dft(unsigned char* bsm) {
     }
 }
 
+// Warpgroups of a tensor-core pass: RT = min(NT, 128) threads own the RT lanes of their tiles;
+// warpgroup w of the CTA takes tiles w, w + NWG, ... (one per group index i of its threads).
+// Each warpgroup stages, issues and drains its own tiles, with its own mbarriers (one per
+// tile index i) and a named barrier, so the tensor core works on one warpgroup's products
+// while others stage or drain theirs, and the products of a warpgroup's tile i overlap the
+// staging of its tile i + 1.
+constexpr int kTcMaxTilesPerGroup = 4;
+constexpr int kTcMaxGroups = 4;
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
+}
+
 template <int RAD, int M, int S, int LC, int NT, bool FWD>
 __device__ __forceinline__ void tc_pass(float2* buf, const float2* tw, TcState& ts) {
     static_assert(NT % S == 0, "thread count must be a multiple of the pass stride");
     static_assert(RAD == 8 || RAD == 16, "tensor-core passes are radix 8 or 16");
     using V = float2;
     constexpr int G = LC / RAD;            // groups: one TMEM lane (row of A and D) each
-    constexpr int J = G / NT;              // groups per thread
-    constexpr int RT = tc_rows(NT);        // rows per tile
+    constexpr int J = G / NT;              // groups (tiles) per thread
+    constexpr int RT = tc_rows(NT);        // rows per tile = threads per warpgroup
+    constexpr int NWG = NT / RT;           // warpgroups
     constexpr int CT = 4 * RAD;            // TMEM columns per tile: hi, lo (RAD each), D (2 RAD)
-    constexpr int T = G / RT;              // tiles
     constexpr int N = 2 * RAD;             // MMA N (and K of one operand part)
     constexpr int NCH = N / 16;            // K = 16 chunks per part
     constexpr uint32_t KST = (N / 8) * 128;   // bytes between K-adjacent core matrices of W
     constexpr uint32_t BM = N * N * 2;
-    static_assert(J >= 1 && G % NT == 0 && G % RT == 0, "groups must divide over threads");
+    static_assert(J >= 1 && G % NT == 0 && NT % RT == 0, "groups must divide over threads");
+    static_assert(J <= kTcMaxTilesPerGroup && NWG <= kTcMaxGroups, "mbarrier slots");
     const int tid = threadIdx.x;
+    const int wg = tid / RT;
+    const bool leader = (tid % RT) == 0;
     const uint32_t lane_base = (uint32_t)(32 * ((tid >> 5) & 3)) << 16;
-    V wp[RAD];
-    powers<RAD>(tw[S + tid % S], wp);
-    // 1. split rows into TMEM (inverse: conjugate twiddles first)
+    V wp[RAD];  // twiddle powers: used before the products (inverse) or after (forward)
+    if constexpr (!FWD) powers<RAD>(tw[S + tid % S], wp);
+    // 1. per tile: split rows into TMEM (inverse: conjugate twiddles first), then the
+    //    warpgroup's leader issues the three split products and commits to the tile's mbarrier
 #pragma unroll 1
     for (int i = 0; i < J; ++i) {
         const int g = tid + i * NT;
         const int t = g / RT;
         const int base = (g / S) * M + (g % S);
-        uint32_t hi[RAD], lo[RAD];
-#pragma unroll
-        for (int q = 0; q < RAD; ++q) {
-            V x = buf[sidx<V>(base + q * S)];
-            if (!FWD && q > 0) x = cmulc(x, wp[q]);
-            tc::split2(x.x, x.y, hi[q], lo[q]);
-        }
         const uint32_t col = ts.tmem + lane_base + (uint32_t)(t * CT);
-        if constexpr (RAD == 16) {
-            tc::tmem_st16(col, hi);
-            tc::tmem_st16(col + RAD, lo);
-        } else {
-            tc::tmem_st8(col, hi);
-            tc::tmem_st8(col + RAD, lo);
+        // eight points at a time (hi to columns [q0, q0 + 8), lo to [RAD + q0, ...))
+#pragma unroll
+        for (int q0 = 0; q0 < RAD; q0 += 8) {
+            uint32_t hi[8], lo[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                V x = buf[sidx<V>(base + (q0 + q) * S)];
+                if (!FWD && q0 + q > 0) x = cmulc(x, wp[q0 + q]);
+                tc::split2(x.x, x.y, hi[q], lo[q]);
+            }
+            tc::tmem_st8(col + q0, hi);
+            tc::tmem_st8(col + RAD + q0, lo);
         }
-    }
-    tc::tmem_wait_st();
-    tc::fence_before_sync();
-    __syncthreads();
-    // 2. one thread issues the three split products of every tile
-    if (tid == 0) {
-        tc::fence_after_sync();
-        constexpr uint32_t idesc = tc::idesc_bf16(128, N);
-        const uint32_t wh = ts.bsm + (FWD ? 0u : 2u * BM), wl = wh + BM;
-#pragma unroll 1
-        for (int t = 0; t < T; ++t) {
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        named_barrier(1 + wg, RT);
+        if (leader && !ts.stall) {
+            tc::fence_after_sync();
+            constexpr uint32_t idesc = tc::idesc_bf16(128, N);
+            const uint32_t wh = ts.bsm + (FWD ? 0u : 2u * BM), wl = wh + BM;
             const uint32_t a = ts.tmem + (uint32_t)(t * CT);
             const uint32_t d = a + 2 * RAD;
 #pragma unroll
@@ -398,19 +417,20 @@ __device__ __forceinline__ void tc_pass(float2* buf, const float2* tw, TcState& 
 #pragma unroll
             for (int c = 0; c < NCH; ++c)
                 tc::mma_ts(d, a + 8 * c, tc::smem_desc(wl + c * 2 * KST, KST, 128), idesc, 1u);
+            tc::mma_commit(ts.mbar + 8u * (uint32_t)(wg * kTcMaxTilesPerGroup + i));
         }
-        tc::mma_commit(ts.mbar);
     }
-    // 3. wait for the products (bounded), read D, twiddle (forward), store
-    if (!*ts.fail && !tc::mbar_wait_bounded(ts.mbar, ts.phase, kTcWaitNs)) {
-        *ts.fail = 1;
-        if (ts.status) atomicOr(ts.status, TDH_STATUS_TIMEOUT);
-    }
-    ts.phase ^= 1u;
-    __syncwarp();
-    tc::fence_after_sync();
+    // 2. per tile: wait for its products (bounded), read D, twiddle (forward), store
+    if constexpr (FWD) powers<RAD>(tw[S + tid % S], wp);
 #pragma unroll 1
     for (int i = 0; i < J; ++i) {
+        const uint32_t mb = ts.mbar + 8u * (uint32_t)(wg * kTcMaxTilesPerGroup + i);
+        if (!*ts.fail && !tc::mbar_wait_bounded(mb, ts.phase, kTcWaitNs)) {
+            *ts.fail = 1;
+            if (ts.status) atomicOr(ts.status, TDH_STATUS_TIMEOUT);
+        }
+        __syncwarp();
+        tc::fence_after_sync();
         const int g = tid + i * NT;
         const int t = g / RT;
         const int base = (g / S) * M + (g % S);
@@ -427,6 +447,7 @@ __device__ __forceinline__ void tc_pass(float2* buf, const float2* tw, TcState& 
             buf[sidx<V>(base + p * S)] = y;
         }
     }
+    ts.phase ^= 1u;
     tc::fence_before_sync();
 }
 
@@ -520,6 +541,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 #pragma unroll 1
     for (int64_t r = r_begin; r < r_end; ++r) {
         const V* ur = P.u + ((int64_t)r * C + k1) * P.u_stride;
+        const T cpair = (P.full && P.pair_c) ? P.pair_c[r] : T(1);
         // ---- forward pass 0: inputs u_r o v (upper half zero), radix R, stride S0
         V ul0[J0][R / 2];  // the factor values of every group first: one L2 latency
 #pragma unroll
@@ -687,7 +709,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             for (int q = 0; q < R / 2; ++q) {
                 const V uu = ul[q];
                 if (P.full) {
-                    acc[j][q].x = fma(uu.y, x[q].y, fma(uu.x, x[q].x, acc[j][q].x));
+                    acc[j][q].x = fma(uu.y * cpair, x[q].y, fma(uu.x, x[q].x, acc[j][q].x));
                 } else {
                     acc[j][q].x = fma(uu.x, x[q].x, acc[j][q].x);
                     acc[j][q].y = fma(uu.y, x[q].y, acc[j][q].y);
@@ -793,7 +815,7 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
     // tensor-core passes: DFT matrices in shared memory, TMEM for A and D, one mbarrier
     constexpr int TCOLS = tc_cols(LOGLC, R, NT);
     __shared__ uint32_t tc_slot;
-    __shared__ __align__(8) uint64_t tc_mbar;
+    __shared__ __align__(8) uint64_t tc_mbar[TC ? kTcMaxGroups * kTcMaxTilesPerGroup : 1];
     __shared__ int tc_fail;
     TcState tcs{};
     if constexpr (TC) {
@@ -804,8 +826,8 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
             tc::tmem_alloc(tc::smem_u32(&tc_slot), TCOLS);
             tc::tmem_relinquish();
         }
+        if (tid < kTcMaxGroups * kTcMaxTilesPerGroup) tc::mbar_init(tc::smem_u32(&tc_mbar[tid]), 1);
         if (tid == 0) {
-            tc::mbar_init(tc::smem_u32(&tc_mbar), 1);
             tc::mbar_fence_init();
             tc_fail = 0;
         }
@@ -814,10 +836,11 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
         tc::fence_after_sync();
         tcs.tmem = tc_slot;
         tcs.bsm = tc::smem_u32(bsm);
-        tcs.mbar = tc::smem_u32(&tc_mbar);
+        tcs.mbar = tc::smem_u32(&tc_mbar[0]);
         tcs.phase = 0;
         tcs.fail = &tc_fail;
         tcs.status = P.status;
+        tcs.stall = P.tc_stall;
     }
     if constexpr (!RAGGED) {
         const int64_t G = gridDim.x / C;
@@ -909,7 +932,6 @@ constexpr size_t exec_smem() {
 template <typename T, int LOGLC, int R, int C, int NT, int MINB, bool RAGGED, bool TC>
 int launch_inst(const ExecParams<T>& P0, int64_t batch, cudaStream_t s) {
     using V = typename cx<T>::t;
-    constexpr PassGeom G{LOGLC, R};
     constexpr size_t smem = exec_smem<V, LOGLC, R, NT, TC>();
     static_assert(smem <= 232448, "shared memory budget");
     static_assert(!TC || tc_cols(LOGLC, R, NT) <= 512, "tensor memory budget");

@@ -48,6 +48,9 @@ int sm_count();
 // test hook that makes the k-th allocation from now fail (k = 0: none).
 void alloc_stats(int64_t* out);
 void fail_alloc_after(int64_t k);
+// Test hook: while set, tensor-core passes issue no products (their bounded waits run out).
+int tc_stall_enabled();
+void set_tc_stall(int on);
 
 // One-time set-up per device (kernel attributes, occupancy queries): `f(int* val)` returns a
 // cudaError_t and runs once for each device that is current when it is needed; its result
@@ -110,6 +113,7 @@ struct Geometry {
     int NT;     // threads per CTA
     int MINB;   // CTAs per SM the kernel's registers are capped for (launch bounds)
     int tc;     // 1: middle passes as split-bfloat16 tensor-core DFT products (TDH_BF16X3)
+    int tma;    // multi-pass, 16 <= C <= 256: the cross stage's block moved by TMA copies
 };
 
 // Device data of one execute configuration.
@@ -168,6 +172,13 @@ struct Step {
     void* d2x = nullptr;
     void* row0 = nullptr;  // CHEB2LEG: row 0 of A in execute precision, else null
     ExecData ex;
+    // rank-pair packing (full): the terms of pair p are pair_idx[2p] and pair_idx[2p+1] (sorted
+    // by max_k |u_r[k] D2_k|), the second scaled by pair_s[p] on the way in and its output by
+    // pair_c[p] = 1 / pair_s[p]^2 (execute precision), so both halves of the packed complex FFT
+    // carry comparable magnitudes and neither's rounding swamps the other
+    int* pair_idx = nullptr;
+    double* pair_s = nullptr;
+    void* pair_c = nullptr;
     // ragged batches: one execute configuration per FFT length 2^(8+i), sharing u_nat
     std::vector<ExecData> rcls;
     void* u_nat = nullptr;  // [K][ceil(n/2)] packed factor pairs in execute precision

@@ -11,6 +11,7 @@
 //   mp_inv   : inverse local DIT passes, W[b][k1][k2] += u_r o y
 // then beta = D1 W (D2 for the adjoint).  Scratch (v, Y, W) is stream-ordered
 // (the library's stream-ordered pool) and vectors are processed in chunks that bound it.
+#include <cuda.h>
 #include <algorithm>
 #include <mutex>
 
@@ -40,6 +41,8 @@ struct MPParams {
     V* Y;     // [B][C][LC]
     V* W;     // [B][C][LC/2]
     T* r0;    // [B] row-0 sum (forward) or g_0 (adjoint)
+    const T* pair_c;  // rank-pair packing: output factor of each pair's second term
+    int* status;      // the plan's device status word (a TMA wait that ran out)
 };
 
 constexpr int kEw = 256;
@@ -217,6 +220,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T
     const int k1 = blockIdx.x % P.C;
     pdl_trigger();
     const V* ur = P.u + (r * P.C + k1) * (LC / 2);
+    const T cpair = (P.full && P.pair_c) ? P.pair_c[r] : T(1);
     V* w = P.W + (bl * P.C + k1) * (LC / 2);
     // the factor and accumulator slices of the last pass, on their way to L2 meanwhile
     prefetch_l2(ur, (int)sizeof(V) * (LC / 2));
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T
             const V uu = ul[q];
             V acc = wl[q];
             if (P.full) {
-                acc.x = fma(uu.y, x[q].y, fma(uu.x, x[q].x, acc.x));
+                acc.x = fma(uu.y * cpair, x[q].y, fma(uu.x, x[q].x, acc.x));
             } else {
                 acc.x = fma(uu.x, x[q].x, acc.x);
                 acc.y = fma(uu.y, x[q].y, acc.y);
@@ -456,6 +460,201 @@ __global__ void __launch_bounds__(256) mp_cross16(const MPParams<T> P) {
     }
 }
 
+// The same cross stage with the block of Y it works on (C slices x PP positions) moved by the
+// tensor memory accelerator: one bulk tensor copy in, issued by one thread once the previous
+// kernel's writes are visible, while the others form their twiddles; one bulk copy out.  The
+// block stays in shared memory in the copy's own layout, slice-major ([C][PP], or
+// [NX][C][PP / NX] when a row exceeds the 256-element box limit): every phase reads
+// consecutive positions on consecutive lanes, so no padding is needed.
+constexpr uint64_t kTmaWaitNs = 1000000000ull;
+
+template <typename T, int LC, int C>
+__global__ void __launch_bounds__(256) mp_cross16_tma(const MPParams<T> P,
+                                                      const __grid_constant__ CUtensorMap tmap) {
+    using V = typename cx<T>::t;
+    constexpr int NTH = 256, PP = 4096 / C, C2 = C / 16;
+    constexpr int XE = PP * (int)sizeof(V) / 8;  // 8-byte elements per row of the block
+    constexpr int NX = XE > 256 ? XE / 256 : 1;  // copies along x (box rows <= 256 elements)
+    constexpr int PX = PP / NX;                  // positions per copy
+    static_assert(C >= 16 && C <= 256 && LC % PP == 0 && PP * C2 == NTH, "cross-stage shape");
+    static_assert(PX * NX == PP && PX * (int)sizeof(V) % 16 == 0, "TMA box rows");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    V* tile = reinterpret_cast<V*>(smem_raw);  // the block: element (k1, p) at tix(k1, p)
+    V* twc = tile + C * PP;                    // omega_C^k, k < C
+    constexpr bool kKeepW = sizeof(T) == 8;    // float64 keeps the phase-A twiddles (see above)
+    V* wt = twc + C;
+    auto tix = [](int k1, int p) { return (p / PX) * (C * PX) + k1 * PX + (p % PX); };
+    __shared__ __align__(8) uint64_t mbar;
+    const int tid = threadIdx.x;
+    const int64_t bl = blockIdx.y;
+    const int pos0 = blockIdx.x * PP;
+    if (tid == 0) {
+        tc::mbar_init(tc::smem_u32(&mbar), 1);
+        tc::mbar_fence_init();
+    }
+    pdl_trigger();
+    for (int k = tid; k < C; k += NTH)
+        twc[k] = omega_L(P.thi, P.tlo, (int64_t)k * (P.L / C), P.L, P.shift);
+    __syncthreads();  // the mbarrier is initialised
+    pdl_wait();       // Y was written by the previous kernel
+    if (tid == 0) {
+        tc::mbar_arrive_expect_tx(tc::smem_u32(&mbar), (uint32_t)(C * PP * sizeof(V)));
+        for (int i = 0; i < NX; ++i)
+            tc::tma_load_3d(tc::smem_u32(tile + i * C * PX), &tmap,
+                            (pos0 + i * PX) * (int)sizeof(V) / 8, 0, (int)bl,
+                            tc::smem_u32(&mbar));
+    }
+    const int pB = tid % PP, aB = tid / PP;
+    const int64_t fpos = P.perm[pos0 + pB];
+    V w[16];  // omega_L^{k1 fpos}, k1 = aB + C2 i, formed while the copy is in flight
+    if constexpr (sizeof(T) == 4) {
+        const V wb = omega_L(P.thi, P.tlo, (int64_t)aB * fpos, P.L, P.shift);
+        powers<16>(omega_L(P.thi, P.tlo, (int64_t)C2 * fpos, P.L, P.shift), w);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) w[i] = cmul(wb, w[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            w[i] = omega_L(P.thi, P.tlo, (int64_t)(aB + C2 * i) * fpos, P.L, P.shift);
+    }
+    if (!tc::mbar_wait_bounded(tc::smem_u32(&mbar), 0, kTmaWaitNs) && P.status)
+        atomicOr(P.status, TDH_STATUS_TIMEOUT);
+    // phase A: twiddles in place
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int e = tix(aB + C2 * i, pB);
+        tile[e] = cmul(tile[e], w[i]);
+        if constexpr (kKeepW) wt[e] = w[i];
+    }
+    __syncthreads();
+    // phases B and D: one (position, a) per thread
+    {
+        V x[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) x[b] = tile[tix(aB + C2 * b, pB)];
+        dif<16>(x);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+            const int c = bitrev(jj, 16);
+            tile[tix(aB + C2 * c, pB)] = (aB * c == 0) ? x[jj] : cmul(x[jj], twc[aB * c]);
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int g = tid; g < PP * 16; g += NTH) {
+        const int p = g % PP, c = g / PP;
+        const int64_t pos = pos0 + p;
+        V x[C2];
+#pragma unroll
+        for (int a = 0; a < C2; ++a) x[a] = tile[tix(a + C2 * c, p)];
+        dif<C2>(x);
+#pragma unroll
+        for (int jj = 0; jj < C2; ++jj) {
+            const V sv = P.spec[(int64_t)(c + 16 * bitrev(jj, C2)) * LC + pos];
+            x[jj] = P.adjoint ? cmulc(x[jj], sv) : cmul(x[jj], sv);
+        }
+        dit<C2>(x);
+#pragma unroll
+        for (int a = 0; a < C2; ++a)
+            tile[tix(a + C2 * c, p)] = (a * c == 0) ? x[a] : cmulc(x[a], twc[a * c]);
+    }
+    __syncthreads();
+    {
+        V x[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) x[jj] = tile[tix(aB + C2 * bitrev(jj, 16), pB)];
+        dit<16>(x);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) tile[tix(aB + C2 * b, pB)] = x[b];
+    }
+    __syncthreads();
+    // phase E: conjugate twiddles in place, then the block back to Y
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int e = tix(aB + C2 * i, pB);
+        tile[e] = cmulc(tile[e], kKeepW ? wt[e] : w[i]);
+    }
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+        for (int i = 0; i < NX; ++i)
+            tc::tma_store_3d(&tmap, (pos0 + i * PX) * (int)sizeof(V) / 8, 0, (int)bl,
+                             tc::smem_u32(tile + i * C * PX));
+        tc::bulk_commit_group();
+        tc::bulk_wait_all();  // the writes are complete before the next kernel may start
+    }
+}
+
+// cuTensorMapEncodeTiled from the driver (through the runtime; the library links no driver
+// library), looked up once.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of a chunk's Y, [nb][C][LC] complex values, as 8-byte elements: x = position
+// (times sizeof(V) / 8), y = slice, z = vector; box = (PX positions, C slices, 1 vector).
+template <typename T>
+int cross_tensor_map(const MPParams<T>& Q, int LC, int64_t nb, CUtensorMap* tm) {
+    using V = typename cx<T>::t;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return TDH_ERR_UNSUPPORTED;
+    }
+    const int PP = 4096 / Q.C;
+    const int XE = PP * (int)sizeof(V) / 8;
+    const int NX = XE > 256 ? XE / 256 : 1;
+    const cuuint64_t dims[3] = {(cuuint64_t)LC * sizeof(V) / 8, (cuuint64_t)Q.C, (cuuint64_t)nb};
+    const cuuint64_t strides[2] = {(cuuint64_t)LC * sizeof(V), (cuuint64_t)Q.C * LC * sizeof(V)};
+    const cuuint32_t box[3] = {(cuuint32_t)(XE / NX), (cuuint32_t)Q.C, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, Q.Y, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return TDH_ERR_CUDA;
+    }
+    return TDH_OK;
+}
+
+template <typename T, int LC, int C>
+int cross16_tma_launch(const MPParams<T>& Q, int64_t nb, const CUtensorMap& tm, cudaStream_t s) {
+    using V = typename cx<T>::t;
+    constexpr int PP = 4096 / C;
+    constexpr size_t smem = (size_t)((sizeof(T) == 8 ? 2 : 1) * PP * C + C) * sizeof(V);
+    static PerDevice attr_once;
+    const cudaError_t err = per_device(attr_once, [&](int*) {
+        return cudaFuncSetAttribute(mp_cross16_tma<T, LC, C>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    cudaError_t e = err;
+    if (e == cudaSuccess)
+        e = launch_pdl(mp_cross16_tma<T, LC, C>, dim3(LC / PP, (unsigned)nb), dim3(256), smem, s,
+                       Q, tm);
+    if (e != cudaSuccess) {
+        set_error("multi-pass cross stage (TMA): %s", cudaGetErrorString(e));
+        return TDH_ERR_CUDA;
+    }
+    note_launches(1);
+    return TDH_OK;
+}
+
 template <typename T, int LC, int C>
 int cross16_launch(const MPParams<T>& Q, int64_t nb, cudaStream_t s) {
     using V = typename cx<T>::t;
@@ -480,9 +679,21 @@ int cross16_launch(const MPParams<T>& Q, int64_t nb, cudaStream_t s) {
     return TDH_OK;
 }
 
-// The cross stage for one rank term of a chunk of nb vectors.
+// The cross stage for one rank term of a chunk of nb vectors (tm: the chunk's tensor map
+// when the schedule moves the block by TMA, else null).
 template <typename T, int LC>
-int cross_launch(const MPParams<T>& Q, int64_t nb, size_t smem_cross, cudaStream_t s) {
+int cross_launch(const MPParams<T>& Q, int64_t nb, size_t smem_cross, const CUtensorMap* tm,
+                 cudaStream_t s) {
+    if (tm) {
+        switch (Q.C) {
+        case 16: return cross16_tma_launch<T, LC, 16>(Q, nb, *tm, s);
+        case 32: return cross16_tma_launch<T, LC, 32>(Q, nb, *tm, s);
+        case 64: return cross16_tma_launch<T, LC, 64>(Q, nb, *tm, s);
+        case 128: return cross16_tma_launch<T, LC, 128>(Q, nb, *tm, s);
+        case 256: return cross16_tma_launch<T, LC, 256>(Q, nb, *tm, s);
+        default: break;
+        }
+    }
     switch (Q.C) {
     case 16: return cross16_launch<T, LC, 16>(Q, nb, s);
     case 32: return cross16_launch<T, LC, 32>(Q, nb, s);
@@ -557,6 +768,8 @@ int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjo
     P.din = static_cast<const T*>(adjoint ? st.d1x : st.d2x);
     P.dout = static_cast<const T*>(adjoint ? st.d2x : st.d1x);
     P.row0 = static_cast<const T*>(st.row0);
+    P.pair_c = static_cast<const T*>(st.pair_c);
+    P.status = st.status;
 
     // chunk the batch so the scratch stays below ~2 GB
     const size_t per_vec = sizeof(V) * (size_t)P.L * 2 + sizeof(T);
@@ -600,10 +813,13 @@ int run_typed(const Step& st, const void* in, void* out, int64_t batch, int adjo
         note_launches(P.row0 ? 2 : 1);
         cudaError_t e = cudaSuccess;
         const dim3 gp((unsigned)(nb * P.C)), bp(NT);
+        CUtensorMap tm;
+        const bool use_tma = ex.g.tma && P.C >= 16 && P.C <= 256;
+        if (use_tma) rc = cross_tensor_map<T>(Q, LC, nb, &tm);
         for (int64_t r = 0; rc == TDH_OK && e == cudaSuccess && r < P.K; ++r) {
             e = launch_pdl(mp_fwd<T, LOGLC, R, NT>, gp, bp, smem_pass, s, Q, r);
             if (e != cudaSuccess) break;
-            rc = cross_launch<T, LC>(Q, nb, smem_cross, s);
+            rc = cross_launch<T, LC>(Q, nb, smem_cross, use_tma ? &tm : nullptr, s);
             if (rc != TDH_OK) break;
             e = launch_pdl(mp_inv<T, LOGLC, R, NT>, gp, bp, smem_pass, s, Q, r);
             if (e == cudaSuccess) note_launches(2);

@@ -1,7 +1,7 @@
-// Blackwell tensor-core building blocks (sm_100 family, tcgen05) for the split-bfloat16 DFT
-// passes of the execute kernels: tensor-memory (TMEM) allocation, loads and stores, the
-// bfloat16 MMA with its A operand in tensor memory and B in shared memory, completion through
-// an mbarrier with a bounded wait.
+// Blackwell building blocks (sm_100 family) for the execute kernels: tensor-memory (TMEM)
+// allocation, loads and stores and the bfloat16 MMA (tcgen05) of the split-bfloat16 DFT passes,
+// with its A operand in tensor memory and B in shared memory; bulk tensor copies (TMA) of the
+// multi-pass cross stage; completion through mbarriers with a bounded wait.
 //
 // Conventions used here (PTX ISA, tcgen05 section):
 //   * a TMEM address is (lane << 16) | column; an allocation starts at lane 0;
@@ -162,15 +162,57 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// try_wait that lets the hardware suspend the thread until the phase completes or about
+// `hint_ns` pass (instead of returning at once), so waiting warps do not spin on the issue slots.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t mbar, uint32_t parity,
+                                                   uint32_t hint_ns) {
+    uint32_t ok = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(mbar), "r"(parity), "r"(hint_ns) : "memory");
+    return ok != 0;
+}
 // Wait for phase `parity` of the mbarrier for at most `limit_ns`; false if the limit passed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity,
                                                   uint64_t limit_ns) {
     if (mbar_try_wait(mbar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
-    while (!mbar_try_wait(mbar, parity)) {
+    while (!mbar_try_wait_hint(mbar, parity, 100000u)) {
         if (globaltimer_ns() - t0 > limit_ns) return false;
     }
     return true;
+}
+
+// ---------------------------------------------------------------- TMA (bulk tensor copies)
+// The mbarrier expects `bytes` more bytes of asynchronous copies (and gets this thread's
+// arrival).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(mbar), "r"(bytes) : "memory");
+}
+// Box at coordinates (x, y, z) of the 3-D tensor map `tmap` (a __grid_constant__ parameter)
+// into shared memory at `dst`; completion counted on the mbarrier.  x * element size must be a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int x, int y, int z,
+                                            uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
+}
+// Shared memory at `src` to the box at (x, y, z) (bulk group of this thread).
+__device__ __forceinline__ void tma_store_3d(const void* tmap, int x, int y, int z, uint32_t src) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+        :: "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(src) : "memory");
+}
+__device__ __forceinline__ void bulk_commit_group() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until every bulk group of this thread has completed (its global writes done).
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------- split bfloat16

@@ -10,7 +10,8 @@ same rounding grows with them (normwise: u max|A_jk| ||alpha||_1), and the outpu
 exceed tol / u ||alpha||_1, past which even its own final rounding breaks tol ||alpha||_1.
 The tests therefore check
 
-    max |beta - beta_ref| <= tol ||alpha||_1 kappa,   kappa = max(1, max_{j,k < 512} |A_jk|)
+    max |beta - beta_ref| <= tol ||alpha||_1 kappa,
+    kappa = max(1, ||beta_ref||_inf / ||alpha||_1, max_{j,k < 512} |A_jk|)
 
 for every conversion with a Toeplitz-dot-Hankel step.  Conversions made of Case-1 steps only
 (integer parameter differences, Sec. 5.2, 5.3: banded factors and back-substitution) round

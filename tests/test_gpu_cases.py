@@ -5,11 +5,11 @@ end, against the dense oracle (whose closed forms are pinned by exact rationals)
 
 Every check is max|beta - beta_ref| <= tol ||alpha||_1 kappa with the stated tolerances
 (float64 1e-12, float32 5e-6) and the conversion's conditioning factor kappa
-(tests/conditioning.py): 1 for conversions that raise every parameter, so the stated bound
-holds as is; the largest entry max|A_jk| for those that lower one through a
-Toeplitz-dot-Hankel step, whose fast product errs in proportion to it; and for conversions
-of Case-1 steps only, max(1, ||beta_ref||_inf / ||alpha||_1), the output's own size.  Plans
-are accuracy-targeted at half that bound.  Ultraspherical 20.5 -> 0.5 produces
+(tests/conditioning.py): 1 for conversions that raise every parameter (their outputs stay
+below ||alpha||_1), so the stated bound holds as is; otherwise the output's own size
+||beta_ref||_inf / ||alpha||_1, and for conversions with a Toeplitz-dot-Hankel step also the
+largest entry max|A_jk|, in proportion to which the fast product errs.  Plans are
+accuracy-targeted at half the stated tolerance.  Ultraspherical 20.5 -> 0.5 produces
 coefficients near 1e102, beyond float32: float64 only.
 """
 import numpy as np
@@ -41,17 +41,21 @@ def _err(y, ref, alpha):
 
 
 def _bound(kind, params, prec, alpha=None, ref=None):
-    """tol ||alpha||_1 kappa / ||alpha||_1: the conversion's conditioning factor (largest
-    entry; for Case-1-only conversions the output's size) times the stated tolerance."""
+    """tol kappa: the stated tolerance times the conversion's conditioning factor (the
+    output's own size, and for conversions with a Toeplitz-dot-Hankel step also the largest
+    entry of the matrix), per unit of ||alpha||_1."""
+    out = output_kappa(alpha, ref) if ref is not None else 1.0
     if case1_only(kind, params):
-        return TOL[prec] * (output_kappa(alpha, ref) if ref is not None else 1.0)
-    return TOL[prec] * kappa(kind, tuple(params))
+        return TOL[prec] * out
+    return TOL[prec] * max(out, kappa(kind, tuple(params)))
 
 
 def _execute(tdh, kind, params, alpha, prec, adjoint=False):
+    """Accuracy-targeted plan at half the stated tolerance (each Toeplitz-dot-Hankel step's
+    truncation), the default of the Python binding."""
     import torch
-    plan = tdh.Plan(kind, alpha.shape[-1], prec=prec, tol=0.5 * _bound(kind, params, prec),
-                    target=True, params=params)
+    plan = tdh.Plan(kind, alpha.shape[-1], prec=prec, tol=0.5 * TOL[prec], target=True,
+                    params=params)
     x = torch.tensor(alpha, dtype=plan.dtype, device="cuda")
     y = plan.adjoint(x) if adjoint else plan.execute(x)
     torch.cuda.synchronize()

@@ -1,10 +1,15 @@
-"""Failure detection on the host: device allocations that fail (tdh_test_fail_alloc).
+"""Failure detection without a GPU fault.
 
-The library's every device allocation goes through two functions (plan memory and execute
-scratch).  The test hook makes the k-th of them fail on the host, as an out-of-memory
-cudaMalloc would, without touching the GPU.  Each entry point must then return
-TDH_ERR_NOMEM with a message and give back everything it had allocated
-(tdh_alloc_stats counts the blocks held).  No GPU fault is involved.
+Allocation failures (tdh_test_fail_alloc): the library's every device allocation goes
+through two functions (plan memory and execute scratch); the hook makes the k-th of them fail
+on the host, as an out-of-memory cudaMalloc would.  Each entry point must then return
+TDH_ERR_NOMEM with a message and give back everything it had allocated (tdh_alloc_stats
+counts the blocks held).
+
+Device waits (tdh_test_tc_stall): with the hook on, split-bfloat16 kernels issue no
+tensor-core products, so the mbarrier each CTA waits on is never signalled; the wait gives up
+after about a second, the kernel finishes normally and the host reads TIMEOUT from the plan's
+status word.  Nothing traps, faults or hangs.
 """
 import ctypes
 
@@ -140,3 +145,33 @@ def test_pchol_allocation_failure(tdh):
     tdh.inject_alloc_failure(0)
     assert rc == 0, tdh.lib().tdh_last_error()
     assert tdh.alloc_stats()[0] == made
+
+
+def test_tensor_core_wait_times_out_and_reports(tdh):
+    """A split-bfloat16 execute whose tensor-core products are never issued (test hook): every
+    CTA's bounded wait runs out after about a second, the kernel finishes, TIMEOUT is read
+    back on the host, and the context stays usable (the next execute is correct)."""
+    import time
+    import torch
+    import oracle
+    import workloads
+    n = 1000
+    alpha = workloads.coefficients(n, 1, decay=1.0, seed=44)
+    plan = tdh.Plan("leg2cheb", n, prec="bf16x3")
+    x = torch.tensor(alpha, dtype=torch.float32, device="cuda")
+    assert plan.status() == set()
+    tdh.inject_tc_stall(True)
+    try:
+        t0 = time.perf_counter()
+        plan.execute(x)
+        torch.cuda.synchronize()
+        waited = time.perf_counter() - t0
+    finally:
+        tdh.inject_tc_stall(False)
+    assert plan.status() == {"TIMEOUT"}
+    assert 0.5 <= waited <= 30.0, waited
+    y = plan.execute(x)
+    torch.cuda.synchronize()
+    assert plan.status() == set()
+    ref = oracle.matvec(oracle.LEG2CHEB, None, alpha)
+    assert np.abs(y.double().cpu().numpy() - ref).max() / np.abs(alpha).sum() <= 1e-5

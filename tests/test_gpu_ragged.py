@@ -134,3 +134,30 @@ def test_ragged_concurrent_threads(tdh):
     assert not errs, errs
     for o in outs:
         assert torch.equal(o, want)
+
+
+def test_ragged_device_checks(tdh):
+    """Checks that need the device-resident offsets run on the device and are reported by
+    tdh_plan_status: a vector longer than n_max is left unwritten (LENGTH); out overlapping
+    in converts nothing (ALIAS); in == out is rejected on the host."""
+    import torch
+    n = 1000
+    plan = tdh.Plan("leg2cheb", n, prec="fp32", ragged=True)
+    assert plan.status() == set()
+    x = torch.randn(3 * n, device="cuda")
+    y = torch.full_like(x, 7.0)
+    offs = torch.tensor([0, 500, 500 + n + 1, 2 * n + 501], dtype=torch.int64, device="cuda")
+    plan.execute_ragged(x, offs, out=y)
+    assert plan.status() == {"LENGTH"}
+    assert torch.all(y[500:500 + n + 1] == 7.0)  # the over-long vector is left as it was
+    assert plan.status() == set()                # cleared by the read
+    buf = torch.zeros(4 * n, device="cuda")
+    buf[: 2 * n] = torch.randn(2 * n, device="cuda")
+    offs2 = torch.tensor([0, n, 2 * n], dtype=torch.int64, device="cuda")
+    before = buf.clone()
+    plan.execute_ragged(buf[: 2 * n], offs2, out=buf[n:3 * n])
+    assert plan.status() == {"ALIAS"}
+    assert torch.equal(buf, before)
+    with pytest.raises(tdh.TdhError) as e:
+        plan.execute_ragged(buf[: 2 * n], offs2, out=buf[: 2 * n])
+    assert e.value.code == -7

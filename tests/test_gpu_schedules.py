@@ -1,5 +1,6 @@
-"""Every compiled execute schedule (local FFT length, cluster size, threads, CTAs per SM) and
-the autotuner against the oracle (needs a GPU).
+"""Every compiled execute schedule (local FFT length, cluster size, threads, CTAs per SM, and
+for multi-pass lengths the cross stage with or without bulk tensor copies) and the autotuner
+against the oracle (needs a GPU).
 
 A schedule changes only the order of the FFT's floating-point operations, so each one must
 meet the same tolerance (max |beta - beta_ref| / ||alpha||_1: float64 1e-12, float32 5e-6).
@@ -60,13 +61,17 @@ def test_every_schedule(tdh, kind, n, prec):
     x = torch.tensor(alpha, dtype=plan.dtype, device="cuda")
     count = plan.schedules()[0]["count"]
     assert count >= 2, plan.schedules()
+    compiled = tdh.compiled_schedules(prec, plan.schedules()[0]["logL"])
+    assert len(compiled) == count
     seen = set()
     for i in range(count):
         plan.set_schedule(i)
         s = plan.schedules()[0]
         assert s["index"] == i and s["count"] == count, s
         assert (1 << s["logLC"]) * s["C"] == 1 << s["logL"], s
-        seen.add((s["logLC"], s["C"], s["NT"], s["MINB"]))
+        c = compiled[i]
+        assert (c["logLC"], c["C"], c["NT"], c["MINB"]) == (s["logLC"], s["C"], s["NT"], s["MINB"])
+        seen.add((s["logLC"], s["C"], s["NT"], s["MINB"], c["multipass"]))
         y = plan.execute(x)
         g = plan.adjoint(x)
         torch.cuda.synchronize()

@@ -41,6 +41,7 @@ def test_default_schedule_rule(tdh, prec):
             assert (d["logLC"], d["C"]) == (cap, 1 << (logL - cap)), (logL, d)
         elif (1 << (logL - cap)) <= 128:
             assert (d["logLC"], d["C"], d["multipass"]) == (cap - 1, 1 << (logL - cap + 1), 1)
+            assert any(s["multipass"] == 2 for s in sched)  # the TMA variant is a candidate
         else:
             assert (d["logLC"], d["C"], d["multipass"]) == (cap, 1 << (logL - cap), 1)
         assert d["MINB"] == (2 if d["multipass"] and d["logLC"] == cap - 1 else 1)
@@ -52,18 +53,24 @@ def test_every_schedule_is_a_valid_split(tdh, prec, ragged):
     seen_any = 0
     for logL in range(8, (14 if prec == FP32 else 13) + 10):
         sched = tdh.compiled_schedules(prec, logL, ragged)
-        keys = [(s["logLC"], s["C"], s["NT"], s["MINB"]) for s in sched]
+        keys = [(s["logLC"], s["C"], s["NT"], s["MINB"], s["multipass"]) for s in sched]
         assert len(set(keys)) == len(keys), (logL, keys)
         for s in sched:
             seen_any += 1
             lc, C, R, NT = s["logLC"], s["C"], s["R"], s["NT"]
             assert lc + C.bit_length() - 1 == logL, (logL, s)
             assert R == _radix(prec, lc)
-            assert s["multipass"] == (1 if C > 8 else 0)
+            if C > 8:
+                # 2: the cross stage moves its blocks with bulk tensor copies (16 ... 256 slices)
+                assert s["multipass"] in ((1, 2) if C <= 256 else (1,)), s
+            else:
+                assert s["multipass"] == 0
             if ragged:
                 assert C <= 8
             if C > 8:
                 assert 16 <= C <= 512
+                if s["multipass"] == 2:
+                    assert (4096 // C) * (8 if prec == FP32 else 16) % 16 == 0  # box rows
                 continue
             LC, es = 1 << lc, (8 if prec == FP32 else 16)
             S0 = LC // R
