@@ -73,6 +73,7 @@ extern "C" {
 #define TDH_STATUS_TIMEOUT 1 /* a tensor-core pass's bounded wait for its products ran out  */
 #define TDH_STATUS_LENGTH  2 /* a ragged vector was longer than n_max (or offsets decreased) */
 #define TDH_STATUS_ALIAS   4 /* a ragged call's out range overlapped its in range          */
+#define TDH_STATUS_FAULT   8 /* a kernel skipped a bulk copy whose alignment it found wrong  */
 
 /* opaque; after creation only tdh_plan_set_schedule and tdh_plan_autotune change it */
 typedef struct tdh_plan_s* tdh_plan_t;
@@ -244,7 +245,8 @@ int tdh_plan_destroy(tdh_plan_t plan);
  * receives the TDH_STATUS_* bits recorded by the plan's executes so far (any stream), which
  * are then cleared.  TIMEOUT: a split-bfloat16 kernel gave up waiting (after about one
  * second) for its tensor-core products, and the outputs of that execute are not valid.
- * LENGTH, ALIAS: see tdh_plan_execute_ragged.  Synchronises `stream`; executes of interest
+ * FAULT: a multi-pass cross stage found a bulk tensor copy misaligned and skipped it (outputs
+ * not valid; never expected).  LENGTH, ALIAS: see tdh_plan_execute_ragged.  Synchronises `stream`; executes of interest
  * must be complete before it (e.g. enqueued on the same stream).
  * Errors: INVALID_ARG (NULL plan or status), CUDA.
  */

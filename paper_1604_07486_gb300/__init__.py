@@ -204,7 +204,7 @@ class Plan:
         """A^T g for every vector of g (the transpose product)."""
         return self._run(lib().tdh_plan_execute_adjoint, g, out, stream, adjoint=1)
 
-    STATUS = {1: "TIMEOUT", 2: "LENGTH", 4: "ALIAS"}
+    STATUS = {1: "TIMEOUT", 2: "LENGTH", 4: "ALIAS", 8: "FAULT"}
 
     def status(self, stream=None):
         """TDH_STATUS_* bits the plan's kernels recorded since the last call, then cleared

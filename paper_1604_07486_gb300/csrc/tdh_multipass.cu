@@ -479,8 +479,12 @@ __global__ void __launch_bounds__(256) mp_cross16_tma(const MPParams<T> P,
     static_assert(C >= 16 && C <= 256 && LC % PP == 0 && PP * C2 == NTH, "cross-stage shape");
     static_assert(PX * NX == PP && PX * (int)sizeof(V) % 16 == 0, "TMA box rows");
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    V* tile = reinterpret_cast<V*>(smem_raw);  // the block: element (k1, p) at tix(k1, p)
-    V* twc = tile + C * PP;                    // omega_C^k, k < C
+    // bulk tensor copies need a 128-byte aligned shared address; the dynamic region is only
+    // guaranteed 16 (static shared variables come first), so the block starts at the next
+    // 128-byte boundary (the launch reserves 128 bytes for this)
+    const uint32_t pad = (128u - (tc::smem_u32(smem_raw) & 127u)) & 127u;
+    V* tile = reinterpret_cast<V*>(smem_raw + pad);  // the block: (k1, p) at tix(k1, p)
+    V* twc = tile + C * PP;                          // omega_C^k, k < C
     constexpr bool kKeepW = sizeof(T) == 8;    // float64 keeps the phase-A twiddles (see above)
     V* wt = twc + C;
     auto tix = [](int k1, int p) { return (p / PX) * (C * PX) + k1 * PX + (p % PX); };
@@ -497,12 +501,21 @@ __global__ void __launch_bounds__(256) mp_cross16_tma(const MPParams<T> P,
         twc[k] = omega_L(P.thi, P.tlo, (int64_t)k * (P.L / C), P.L, P.shift);
     __syncthreads();  // the mbarrier is initialised
     pdl_wait();       // Y was written by the previous kernel
+    // the copies' alignment rules, checked before any copy is issued (a violation would be
+    // a device fault): 128-byte shared addresses, x offsets in multiples of 16 bytes
+    const bool aligned = (tc::smem_u32(tile) & 127u) == 0 &&
+                         ((pos0 * (int)sizeof(V)) & 15) == 0;
     if (tid == 0) {
-        tc::mbar_arrive_expect_tx(tc::smem_u32(&mbar), (uint32_t)(C * PP * sizeof(V)));
-        for (int i = 0; i < NX; ++i)
-            tc::tma_load_3d(tc::smem_u32(tile + i * C * PX), &tmap,
-                            (pos0 + i * PX) * (int)sizeof(V) / 8, 0, (int)bl,
-                            tc::smem_u32(&mbar));
+        if (aligned) {
+            tc::mbar_arrive_expect_tx(tc::smem_u32(&mbar), (uint32_t)(C * PP * sizeof(V)));
+            for (int i = 0; i < NX; ++i)
+                tc::tma_load_3d(tc::smem_u32(tile + i * C * PX), &tmap,
+                                (pos0 + i * PX) * (int)sizeof(V) / 8, 0, (int)bl,
+                                tc::smem_u32(&mbar));
+        } else {
+            if (P.status) atomicOr(P.status, TDH_STATUS_FAULT);
+            tc::mbar_arrive(tc::smem_u32(&mbar));  // no copy: complete the phase at once
+        }
     }
     const int pB = tid % PP, aB = tid / PP;
     const int64_t fpos = P.perm[pos0 + pB];
@@ -576,12 +589,12 @@ __global__ void __launch_bounds__(256) mp_cross16_tma(const MPParams<T> P,
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && aligned) {
         for (int i = 0; i < NX; ++i)
             tc::tma_store_3d(&tmap, (pos0 + i * PX) * (int)sizeof(V) / 8, 0, (int)bl,
                              tc::smem_u32(tile + i * C * PX));
         tc::bulk_commit_group();
-        tc::bulk_wait_all();  // the writes are complete before the next kernel may start
+        tc::bulk_wait_read();  // shared memory stays valid until the copy has read it
     }
 }
 
@@ -637,7 +650,7 @@ template <typename T, int LC, int C>
 int cross16_tma_launch(const MPParams<T>& Q, int64_t nb, const CUtensorMap& tm, cudaStream_t s) {
     using V = typename cx<T>::t;
     constexpr int PP = 4096 / C;
-    constexpr size_t smem = (size_t)((sizeof(T) == 8 ? 2 : 1) * PP * C + C) * sizeof(V);
+    constexpr size_t smem = (size_t)((sizeof(T) == 8 ? 2 : 1) * PP * C + C) * sizeof(V) + 128;
     static PerDevice attr_once;
     const cudaError_t err = per_device(attr_once, [&](int*) {
         return cudaFuncSetAttribute(mp_cross16_tma<T, LC, C>,

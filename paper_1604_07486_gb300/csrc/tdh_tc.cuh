@@ -191,9 +191,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                  :: "r"(mbar), "r"(bytes) : "memory");
 }
+// Plain arrival on an mbarrier (completes a phase that expects no copies).
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
 // Box at coordinates (x, y, z) of the 3-D tensor map `tmap` (a __grid_constant__ parameter)
-// into shared memory at `dst`; completion counted on the mbarrier.  x * element size must be a
-// multiple of 16 bytes.
+// into shared memory at `dst` (128-byte aligned); completion counted on the mbarrier.
+// x * element size must be a multiple of 16 bytes.
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int x, int y, int z,
                                             uint32_t mbar) {
     asm volatile(
@@ -201,7 +205,7 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int 
         " [%0], [%1, {%2, %3, %4}], [%5];"
         :: "r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(mbar) : "memory");
 }
-// Shared memory at `src` to the box at (x, y, z) (bulk group of this thread).
+// Shared memory at `src` (128-byte aligned) to the box at (x, y, z) (bulk group of this thread).
 __device__ __forceinline__ void tma_store_3d(const void* tmap, int x, int y, int z, uint32_t src) {
     asm volatile(
         "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
@@ -210,9 +214,10 @@ __device__ __forceinline__ void tma_store_3d(const void* tmap, int x, int y, int
 __device__ __forceinline__ void bulk_commit_group() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-// Wait until every bulk group of this thread has completed (its global writes done).
-__device__ __forceinline__ void bulk_wait_all() {
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+// Wait until every bulk group of this thread has finished reading its shared memory (the
+// global writes complete by the end of the grid, before a dependent grid may read them).
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------- split bfloat16

@@ -79,6 +79,7 @@ def test_every_schedule(tdh, kind, n, prec):
         et = _err(g.double().cpu().numpy(), ref_t, alpha, rows)
         assert e <= TOL[prec] and et <= TOL[prec], (s, e, et)
     assert len(seen) == count
+    assert plan.status() == set()  # no bounded wait ran out, no copy was skipped
     # indices past the end take the last schedule
     plan.set_schedule(count + 5)
     assert plan.schedules()[0]["index"] == count - 1

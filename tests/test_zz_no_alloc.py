@@ -39,19 +39,22 @@ def _call(fn, h, n, j0, tol, kmax):
 @pytest.mark.parametrize("kind,j0,n,tol", [("cheb2leg", 1, 65536, 1e-15), ("leg2cheb", 0, 5000, 1e-12)])
 def test_noalloc_matches_allocating_entry(tdh, kind, j0, n, tol):
     """Two calls in a row through the C ABI give the factors tdh_pchol gives (same pivots,
-    same rank, factors within the pivoted-Cholesky test tolerance)."""
+    same rank, factors within the pivoted-Cholesky test tolerance), and the library's
+    allocation counter does not move across them."""
     L = tdh.lib()
     _, h, _, _ = tdh.symbols(kind, n)
     kmax = 128
     rc, K, u_ref, p_ref = _call(L.tdh_pchol, h, n, j0, tol, kmax)
     assert rc == 0 and K >= 10
     scale = np.abs(u_ref).max()
+    made = tdh.alloc_stats()[0]  # device allocations the library has made so far
     for _ in range(2):
         rc, K2, u, p = _call(L.tdh_pchol_noalloc, h, n, j0, tol, kmax)
         assert rc == 0, L.tdh_last_error()
         assert K2 == K
         assert np.array_equal(p, p_ref)
         assert np.abs(u - u_ref).max() <= 1e-9 * scale
+    assert tdh.alloc_stats()[0] == made  # the two calls allocated nothing
 
 
 def test_noalloc_rejects_sizes_beyond_limit(tdh):
