@@ -133,6 +133,23 @@ __host__ __device__ constexpr int tc_cols(int LOGLC, int R, int NT) {
     return c;
 }
 
+// Float32 cluster kernels with one 512-thread CTA per SM (local FFT 2^14) keep the cross
+// stage's spectrum and twiddles -- the same for every rank term and every vector -- in tensor
+// memory, which they do not otherwise use, instead of reading them from L2 for every rank term.
+// Each thread owns one TMEM lane (thread t of warp w: lane 32 (w % 4) + t); per cross-stage
+// iteration it keeps 4 + 4C words (two twiddles, the spectrum of two positions) in a slot of
+// the next power of two; the four warps that share a lane set use 128 columns each.
+template <typename T, int LOGLC, int C, int NT, int MINB, bool TC>
+struct SpecTmem {
+    static constexpr bool on = !TC && std::is_same<T, float>::value && C > 1 && C <= 8 &&
+                               LOGLC == 14 && NT == 512 && MINB == 1;
+    static constexpr int iters = (1 << LOGLC) / C / (2 * NT);  // cross-stage iterations
+    static constexpr int words = 4 + 4 * C;                    // per iteration
+    static constexpr int head = words >= 32 ? 32 : (words >= 16 ? 16 : 8);  // first load width
+    static constexpr int slot = words <= 16 ? 16 : (words <= 32 ? 32 : 64);
+    static_assert(!on || (words - head == 4 && iters * slot == 128), "slot layout");
+};
+
 template <typename T>
 struct ExecParams {
     using V = typename cx<T>::t;
@@ -306,6 +323,7 @@ __device__ __forceinline__ void pass_inv(V* buf, const V* tw) {
 // inverse hi, lo; K-major core-matrix layout), the MMA-completion mbarriers (one per
 // warpgroup and tile) and their common phase.
 struct TcState {
+    uint32_t spec_tmem;  // SpecTmem: base of the cross stage's spectrum and twiddles
     uint32_t tmem;
     uint32_t bsm;
     uint32_t mbar;
@@ -478,7 +496,7 @@ __device__ __forceinline__ void middle_inv(V* buf, const V* twt, TcState* ts) {
 }
 
 // One vector: v = D alpha -> all K rank terms -> beta (the whole of Fig. 1 steps 3-5).
-template <typename T, int LOGLC, int R, int C, int NT, bool TC>
+template <typename T, int LOGLC, int R, int C, int NT, bool TC, bool STM>
 __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* in, T* out,
                                                const int64_t n, const int k1,
                                                typename cx<T>::t* buf, typename cx<T>::t* vbuf,
@@ -632,7 +650,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
                 }
             }
 #pragma unroll 1
-            for (int pi = 2 * tid; kPairs && pi < PPC; pi += 2 * NT) {
+            for (int pi = 2 * tid, it = 0; kPairs && pi < PPC; pi += 2 * NT, ++it) {
                 const int pos = k1 * PPC + pi;  // even: the pair (pos, pos+1) is contiguous
                 const bool swp = pair_swapped<V>(pos);
                 const int sp = sidx<V>(pos) & ~1;
@@ -644,11 +662,33 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
                     a[0][j] = swp ? e1 : e0;
                     a[1][j] = swp ? e0 : e1;
                 }
-                pair_load(P.twx + pos, tw[0], tw[1]);
+                using ST = SpecTmem<T, LOGLC, C, NT, 1, false>;
+                if constexpr (STM) {
+                    // twiddles and spectrum from this thread's tensor-memory slot
+                    const uint32_t col = ts->spec_tmem +
+                                         ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
+                                         (uint32_t)(((tid >> 7) * 128) + it * ST::slot);
+                    uint32_t wh[ST::head], wt[4];
+                    tc::tmem_ld<ST::head>(col, wh);
+                    tc::tmem_ld<4>(col + ST::head, wt);
+                    float fw[ST::words];
 #pragma unroll
-                for (int f = 0; f < C; f += 2) {
-                    pair_load(P.spec + (int64_t)pos * C + f, sc[0][f], sc[0][f + 1]);
-                    pair_load(P.spec + (int64_t)(pos + 1) * C + f, sc[1][f], sc[1][f + 1]);
+                    for (int i = 0; i < ST::words; ++i)
+                        fw[i] = __uint_as_float(i < ST::head ? wh[i] : wt[i - ST::head]);
+                    tw[0] = mk<V>(fw[0], fw[1]);
+                    tw[1] = mk<V>(fw[2], fw[3]);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int f = 0; f < C; ++f)
+                            sc[u][f] = mk<V>(fw[4 + 2 * (u * C + f)], fw[5 + 2 * (u * C + f)]);
+                } else {
+                    pair_load(P.twx + pos, tw[0], tw[1]);
+#pragma unroll
+                    for (int f = 0; f < C; f += 2) {
+                        pair_load(P.spec + (int64_t)pos * C + f, sc[0][f], sc[0][f + 1]);
+                        pair_load(P.spec + (int64_t)(pos + 1) * C + f, sc[1][f], sc[1][f + 1]);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
@@ -842,6 +882,45 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
         tcs.status = P.status;
         tcs.stall = P.tc_stall;
     }
+    // float32 cluster kernels: the cross stage's twiddles and spectrum into tensor memory, once
+    constexpr bool STM = SpecTmem<T, LOGLC, C, NT, MINB, TC>::on;
+    __shared__ uint32_t stm_slot;
+    if constexpr (STM) {
+        using ST = SpecTmem<T, LOGLC, C, NT, MINB, TC>;
+        constexpr int PPC = LC / C;
+        if (tid < 32) {
+            tc::tmem_alloc(tc::smem_u32(&stm_slot), 512);
+            tc::tmem_relinquish();
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tcs.spec_tmem = stm_slot;
+#pragma unroll 1
+        for (int it = 0; it < ST::iters; ++it) {
+            const int pos = k1 * PPC + 2 * tid + it * 2 * NT;
+            // slot words: twiddles of the two positions, then their spectra [u][f]
+            const float* tf = reinterpret_cast<const float*>(P.twx + pos);
+            const float* sf = reinterpret_cast<const float*>(P.spec + (int64_t)pos * C);
+            uint32_t wh[ST::head], wt[4];
+#pragma unroll
+            for (int i = 0; i < ST::words; ++i) {
+                const uint32_t v = __float_as_uint(i < 4 ? tf[i] : sf[i - 4]);
+                if (i < ST::head)
+                    wh[i] = v;
+                else
+                    wt[i - ST::head] = v;
+            }
+            const uint32_t col = tcs.spec_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
+                                 (uint32_t)(((tid >> 7) * 128) + it * ST::slot);
+            tc::tmem_st<ST::head>(col, wh);
+            tc::tmem_st<4>(col + ST::head, wt);
+        }
+        tc::tmem_wait_st();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
     if constexpr (!RAGGED) {
         const int64_t G = gridDim.x / C;
         const int64_t cid = blockIdx.x / C;
@@ -855,7 +934,7 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
             const int64_t r1 = r0 + u1 - u < Ku ? r0 + u1 - u : Ku;
             T* outp = (r0 == 0 && r1 == Ku) ? P.out + vec * P.n
                                             : P.partial + (2 * cid + (r0 == 0 ? 1 : 0)) * P.n;
-            convert_vector<T, LOGLC, R, C, NT, TC>(P, P.in + vec * P.n, outp, P.n, k1, buf, vbuf,
+            convert_vector<T, LOGLC, R, C, NT, TC, STM>(P, P.in + vec * P.n, outp, P.n, k1, buf, vbuf,
                                                    twt, red, r0, r1 < P.K ? r1 : P.K, r0 == 0,
                                                    &tcs);
             u += r1 - r0;
@@ -878,7 +957,7 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
             const int64_t vec = P.list[sidx];
             const int64_t off = P.offs[vec];
             const int64_t n = P.offs[vec + 1] - off;
-            convert_vector<T, LOGLC, R, C, NT, TC>(P, P.in + off, P.out + off, n, k1, buf, vbuf,
+            convert_vector<T, LOGLC, R, C, NT, TC, STM>(P, P.in + off, P.out + off, n, k1, buf, vbuf,
                                                    twt, red, 0, P.K, true, &tcs);
         }
         if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its slot is read
@@ -889,6 +968,14 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
         if (tid < 32) {
             tc::fence_after_sync();
             tc::tmem_dealloc(tcs.tmem, TCOLS);
+        }
+    }
+    if constexpr (STM) {
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid < 32) {
+            tc::fence_after_sync();
+            tc::tmem_dealloc(tcs.spec_tmem, 512);
         }
     }
 }

@@ -60,11 +60,13 @@ def test_every_tensor_core_schedule(tdh, n):
     plan = tdh.Plan(kind, n, prec="bf16x3")
     x = torch.tensor(alpha, dtype=torch.float32, device="cuda")
     count = plan.schedules()[0]["count"]
+    compiled = tdh.compiled_schedules("bf16x3", plan.schedules()[0]["logL"])
+    assert len(compiled) == count
     seen = set()
     for i in range(count):
         plan.set_schedule(i)
         s = plan.schedules()[0]
-        seen.add((s["logLC"], s["C"], s["NT"], s["MINB"]))
+        seen.add((s["logLC"], s["C"], s["NT"], s["MINB"], compiled[i]["multipass"]))
         y = plan.execute(x)
         g = plan.adjoint(x)
         torch.cuda.synchronize()
