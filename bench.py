@@ -722,7 +722,25 @@ def run_extra(args, rank, world, local):
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA " + apeaks["note"] + " (Jacobi multi-pass part)"
         config = {"workload": "jacobi (0.1,-0.3)->(0,0) + ultraspherical 0.25->1.25, n=2^20, batch=16, fp32 execute, fp64 plan, tol 1e-13",
                   "K_jacobi_max_step": pj.K}
-        check = None
+        def check():
+            # the last 512 rows of two vectors exactly: rows j >= j0 of the reflection chain
+            # involve only coefficients k >= j0 at every step (upper triangular), so the
+            # oracle's cost is O(512^2) per vector; the ultraspherical step on sampled rows
+            tail = np.arange(n - 512, n)
+            sign = (-1.0) ** np.arange(n)
+            errs = []
+            yjn = yj[[0, B - 1]].double().cpu().numpy()
+            for b, v in enumerate(alpha[[0, B - 1]]):
+                z = np.zeros(n)
+                z[tail] = sign[tail] * oracle.matvec(oracle.JAC, (-0.3, 0.1, 0.0), sign * v, rows=tail)
+                ref = oracle.matvec(oracle.JAC, (0.1, 0.0, 0.0), z, rows=tail)
+                errs.append(np.abs(yjn[b][tail] - ref).max() / np.abs(v).sum())
+            rows = np.unique(np.r_[np.arange(16), n - 1 - np.arange(16),
+                                   np.random.default_rng(4).integers(0, n, 32)])
+            yun = yu[[0, B - 1]].double().cpu().numpy()
+            refu = oracle.matvec(oracle.ULTRA, (0.25, 1.25), alpha[[0, B - 1]], rows=rows)
+            eu = (np.abs(yun[:, rows] - refu).max(axis=1) / np.abs(alpha[[0, B - 1]]).sum(axis=1)).max()
+            return {"jacobi_last_512_rows": float(max(errs)), "ultraspherical": float(eu)}
         host_in = torch.from_numpy(alpha.astype(np.float32)).pin_memory()
         def host_fn():
             pj.execute(host_in)
