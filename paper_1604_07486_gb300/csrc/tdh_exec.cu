@@ -42,6 +42,9 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
     }
     if (g->C > 512) return false;  // C > 8: multi-pass through global memory
     g->R = radix_for(prec != TDH_FP64, g->logLC);
+    // float32 2^14-point slices of 2-8-CTA clusters: radix 32, 32, 16 (three shared-memory
+    // passes instead of four; their accumulators are in tensor memory)
+    if (prec == TDH_FP32 && g->logLC == 14 && g->C >= 2 && g->C <= 8) g->R = 32;
     g->NT = std::min(512, (1 << g->logLC) / g->R);
     g->MINB = 1;
     if (g->C > 8) mp_threads(prec, g->logLC, &g->NT, &g->MINB);
@@ -51,7 +54,7 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
 
 bool same_schedule(const Geometry& a, const Geometry& b) {
     return a.logLC == b.logLC && a.C == b.C && a.NT == b.NT && a.MINB == b.MINB && a.tc == b.tc &&
-           a.tma == b.tma;
+           a.tma == b.tma && a.R == b.R;
 }
 
 // Every schedule with a compiled kernel for 2^logL points, the default first: the cluster
@@ -62,11 +65,11 @@ std::vector<Geometry> schedule_candidates(int prec, int logL, bool ragged) {
     Geometry d{};
     if (!choose_geometry(prec, logL, &d)) return out;
     out.push_back(d);
-    auto add = [&](int logLC, int C, int NT, int MINB, int tma = 0) {
+    auto add = [&](int logLC, int C, int NT, int MINB, int tma = 0, int R = 0) {
         Geometry g = d;
         g.logLC = logLC;
         g.C = C;
-        g.R = radix_for(prec != TDH_FP64, logLC);
+        g.R = R ? R : radix_for(prec != TDH_FP64, logLC);
         g.NT = NT;
         g.MINB = MINB;
         g.tc = (prec == TDH_BF16X3 && C <= 8) ? 1 : 0;
@@ -83,7 +86,7 @@ std::vector<Geometry> schedule_candidates(int prec, int logL, bool ragged) {
         const Sched e = prec == TDH_BF16X3 ? SchedTableTC::at(i)
                         : f32              ? SchedTable<true>::at(i)
                                            : SchedTable<false>::at(i);
-        if (e.logLC + ilog2(e.C) == logL) add(e.logLC, e.C, e.NT, e.MINB);
+        if (e.logLC + ilog2(e.C) == logL) add(e.logLC, e.C, e.NT, e.MINB, 0, e.R);
     }
     if (!ragged) {
         const int cap = f32 ? 14 : 13;  // (multi-pass kernels: float32 arithmetic for BF16X3)

@@ -76,20 +76,25 @@ __host__ __device__ constexpr int radix_for(bool f32, int logLC) {
     return f32 && logLC > 9 ? 16 : 8;
 }
 
-// Compiled execute schedules: local FFT length 2^logLC, cluster size C, threads per CTA NT and
+// Compiled execute schedules: local FFT length 2^logLC, cluster size C, threads per CTA NT,
 // the occupancy the registers are capped for (MINB CTAs per SM: 65536 / (NT MINB) registers
-// per thread).  The first schedule of each (logLC, C) is the default one; the others trade
-// threads per CTA for CTAs per SM, or local length for cluster size.
+// per thread) and the radix of the local passes (0: radix_for's).  The first schedule of each
+// (logLC, C) is the default one; the others trade threads per CTA for CTAs per SM, local
+// length for cluster size, or four radix-16 passes for three of radix 32, 32 and 16.
 struct Sched {
-    int logLC, C, NT, MINB;
+    int logLC, C, NT, MINB, R = 0;
 };
+__host__ __device__ constexpr int sched_radix(const Sched& e, bool f32) {
+    return e.R ? e.R : radix_for(f32, e.logLC);
+}
 constexpr Sched kSchedF32[] = {
     {8, 1, 32, 1},    {8, 1, 32, 16},   {9, 1, 64, 1},    {9, 1, 64, 8},    {10, 1, 64, 1},
     {10, 1, 64, 8},   {10, 1, 32, 16},  {11, 1, 128, 1},  {11, 1, 128, 4},  {11, 1, 64, 8},
     {12, 1, 256, 1},  {12, 1, 256, 2},  {12, 1, 128, 4},  {13, 1, 512, 1},  {13, 1, 256, 2},
     {14, 1, 512, 1},  {14, 2, 512, 1},  {14, 4, 512, 1},  {14, 8, 512, 1},  {13, 2, 256, 2},
     {13, 4, 256, 2},  {13, 8, 256, 2},  {9, 2, 64, 1},    {8, 4, 32, 1},    {10, 2, 64, 1},
-    {11, 2, 128, 1},  {12, 2, 256, 2},
+    {11, 2, 128, 1},  {12, 2, 256, 2},  {14, 2, 512, 1, 32}, {14, 4, 512, 1, 32},
+    {14, 8, 512, 1, 32},
 };
 constexpr Sched kSchedF64[] = {
     {8, 1, 32, 1},    {8, 1, 32, 16},   {9, 1, 64, 1},    {9, 1, 64, 8},    {10, 1, 128, 1},
@@ -133,12 +138,14 @@ __host__ __device__ constexpr int tc_cols(int LOGLC, int R, int NT) {
     return c;
 }
 
-// Float32 cluster kernels with one 512-thread CTA per SM (local FFT 2^14) keep the cross
-// stage's spectrum and twiddles -- the same for every rank term and every vector -- in tensor
-// memory, which they do not otherwise use, instead of reading them from L2 for every rank term.
-// Each thread owns one TMEM lane (thread t of warp w: lane 32 (w % 4) + t); per cross-stage
-// iteration it keeps 4 + 4C words (two twiddles, the spectrum of two positions) in a slot of
-// the next power of two; the four warps that share a lane set use 128 columns each.
+// Float32 cluster kernels with one 512-thread CTA per SM (local FFT 2^14) keep in tensor
+// memory, which they do not otherwise use: the cross stage's spectrum and twiddles -- the same
+// for every rank term and every vector -- instead of reading them from L2 for every rank term,
+// and the output accumulators w, which otherwise hold 32 registers across the whole rank loop.
+// Each thread owns one TMEM lane (thread t of warp w: lane 32 (w % 4) + t); the four warps
+// that share a lane set take 128 columns each: per cross-stage iteration the first `head` of
+// its 4 + 4C words (two twiddles, the spectrum of two positions) at columns [0, 64), the last 4
+// at [64, 96), the 32 accumulator words at [96, 128).
 template <typename T, int LOGLC, int C, int NT, int MINB, bool TC>
 struct SpecTmem {
     static constexpr bool on = !TC && std::is_same<T, float>::value && C > 1 && C <= 8 &&
@@ -146,8 +153,10 @@ struct SpecTmem {
     static constexpr int iters = (1 << LOGLC) / C / (2 * NT);  // cross-stage iterations
     static constexpr int words = 4 + 4 * C;                    // per iteration
     static constexpr int head = words >= 32 ? 32 : (words >= 16 ? 16 : 8);  // first load width
-    static constexpr int slot = words <= 16 ? 16 : (words <= 32 ? 32 : 64);
-    static_assert(!on || (words - head == 4 && iters * slot == 128), "slot layout");
+    static constexpr int tail_col = 64;                        // columns of the last 4 words
+    static constexpr int acc_col = 96;                         // the accumulators' 32 words
+    static_assert(!on || (words - head == 4 && iters * head == 64 && iters * 4 <= 32),
+                  "slot layout");
 };
 
 template <typename T>
@@ -262,6 +271,51 @@ __device__ __forceinline__ void powers(V w1, V (&wp)[R]) {
     }
 }
 
+// The twiddles w^p, p in [0, R), of one radix-R group.  Up to R = 16 every power is held in
+// registers; for R = 32 (64 registers of data already) only w^0..w^7 and (w^8)^0..(w^8)^3 are,
+// and w^p = (w^8)^(p/8) w^(p%8) costs one product where both factors differ from 1 -- about as
+// many products as the full table, in 24 registers instead of 64.
+template <int R, typename V>
+struct TwPow {
+    static constexpr bool split = R > 16;
+    static constexpr int NL = split ? 8 : R;
+    static constexpr int NH = split ? R / 8 : 1;
+    V lo[NL];
+    V hi[NH];
+    __device__ __forceinline__ explicit TwPow(V w1) {
+        powers<NL>(w1, lo);
+        if constexpr (split) {
+            hi[0] = mk<V>(1, 0);
+            hi[1] = cmul(lo[4], lo[4]);
+#pragma unroll
+            for (int h = 2; h < NH; ++h) hi[h] = (h % 2 == 0) ? cmul(hi[h / 2], hi[h / 2])
+                                                              : cmul(hi[h - 1], hi[1]);
+        }
+    }
+    // x w^p (p a constant after unrolling)
+    __device__ __forceinline__ V mul(V x, int p) const {
+        if constexpr (!split) {
+            return p == 0 ? x : cmul(x, lo[p]);
+        } else {
+            if (p == 0) return x;
+            if (p % 8 == 0) return cmul(x, hi[p / 8]);
+            if (p < 8) return cmul(x, lo[p]);
+            return cmul(x, cmul(hi[p / 8], lo[p % 8]));
+        }
+    }
+    // x conj(w^p)
+    __device__ __forceinline__ V mulc(V x, int p) const {
+        if constexpr (!split) {
+            return p == 0 ? x : cmulc(x, lo[p]);
+        } else {
+            if (p == 0) return x;
+            if (p % 8 == 0) return cmulc(x, hi[p / 8]);
+            if (p < 8) return cmulc(x, lo[p]);
+            return cmulc(x, cmul(hi[p / 8], lo[p % 8]));
+        }
+    }
+};
+
 // Middle forward pass i: radix RAD, sub-length M, stride S, twiddles from the [p][o] table.
 // Every group g = tid + i NT of a thread has the same offset o = g % S (NT is a multiple of
 // S), so its twiddles omega_M^{p o} are powers of one table entry, formed once per pass in
@@ -269,8 +323,7 @@ __device__ __forceinline__ void powers(V w1, V (&wp)[R]) {
 template <int RAD, int M, int S, int LC, int NT, typename V>
 __device__ __forceinline__ void pass_fwd(V* buf, const V* tw) {
     static_assert(NT % S == 0, "thread count must be a multiple of the pass stride");
-    V wp[RAD];
-    powers<RAD>(tw[S + (int)threadIdx.x % S], wp);
+    const TwPow<RAD, V> wp(tw[S + (int)threadIdx.x % S]);
 #pragma unroll 1
     for (int g = threadIdx.x; g < LC / RAD; g += NT) {
         const int b = g / S, o = g % S;
@@ -282,7 +335,7 @@ __device__ __forceinline__ void pass_fwd(V* buf, const V* tw) {
 #pragma unroll
         for (int jj = 0; jj < RAD; ++jj) {
             const int p = bitrev(jj, RAD);
-            buf[sidx<V>(base + p * S)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
+            buf[sidx<V>(base + p * S)] = wp.mul(x[jj], p);
         }
     }
 }
@@ -290,18 +343,14 @@ __device__ __forceinline__ void pass_fwd(V* buf, const V* tw) {
 template <int RAD, int M, int S, int LC, int NT, typename V>
 __device__ __forceinline__ void pass_inv(V* buf, const V* tw) {
     static_assert(NT % S == 0, "thread count must be a multiple of the pass stride");
-    V wp[RAD];
-    powers<RAD>(tw[S + (int)threadIdx.x % S], wp);
+    const TwPow<RAD, V> wp(tw[S + (int)threadIdx.x % S]);
 #pragma unroll 1
     for (int g = threadIdx.x; g < LC / RAD; g += NT) {
         const int b = g / S, o = g % S;
         const int base = b * M + o;
         V x[RAD];
 #pragma unroll
-        for (int p = 0; p < RAD; ++p) {
-            const V y = buf[sidx<V>(base + p * S)];
-            x[bitrev(p, RAD)] = (p == 0) ? y : cmulc(y, wp[p]);
-        }
+        for (int p = 0; p < RAD; ++p) x[bitrev(p, RAD)] = wp.mulc(buf[sidx<V>(base + p * S)], p);
         dit<RAD>(x);
 #pragma unroll
         for (int q = 0; q < RAD; ++q) buf[sidx<V>(base + q * S)] = x[q];
@@ -509,6 +558,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
     constexpr int S0 = LC / R;
     constexpr int J0 = S0 / NT;
     constexpr int RL = G.rad(G.np() - 1);  // radix of the last pass (stride 1)
+    static_assert(R <= 16 || STM, "radix-32 passes need the accumulators in tensor memory");
     const int tid = threadIdx.x;
     T r0acc = T(0);
     for (int k2 = tid; k2 < LC / 2; k2 += NT) {
@@ -540,11 +590,27 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
     V w0[J0];
 #pragma unroll
     for (int j = 0; j < J0; ++j) w0[j] = P.tw0[tid + j * NT];
+    // w accumulators: registers, or (STM) this thread's 32 words of tensor memory, loaded only
+    // around the inverse pass 0 of each rank term and in the epilogue
     V acc[J0][R / 2];
+    constexpr int ACCW = J0 * R;  // float words of the accumulators
+    uint32_t acc_col = 0;
+    if constexpr (STM) {
+        static_assert(ACCW == 32, "tensor-memory accumulators: 32 words per thread");
+        using ST = SpecTmem<T, LOGLC, C, NT, 1, false>;
+        acc_col = ts->spec_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
+                  (uint32_t)((tid >> 7) * 128 + ST::acc_col);
+        uint32_t z[32];
 #pragma unroll
-    for (int j = 0; j < J0; ++j)
+        for (int i = 0; i < 32; ++i) z[i] = 0u;
+        tc::tmem_st<32>(acc_col, z);
+        tc::tmem_wait_st();
+    } else {
 #pragma unroll
-        for (int q = 0; q < R / 2; ++q) acc[j][q] = mk<V>(0, 0);
+        for (int j = 0; j < J0; ++j)
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) acc[j][q] = mk<V>(0, 0);
+    }
     __syncthreads();
 
     V* rbuf[C];
@@ -573,12 +639,11 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) x[q] = cwmul(vbuf[o + q * S0], ul0[j][q]);
             dif_halfzero<R>(x);
-            V wp[R];
-            powers<R>(w0[j], wp);
+            const TwPow<R, V> wp(w0[j]);
 #pragma unroll
             for (int jj = 0; jj < R; ++jj) {
                 const int p = bitrev(jj, R);
-                buf[sidx<V>(o + p * S0)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
+                buf[sidx<V>(o + p * S0)] = wp.mul(x[jj], p);
             }
         }
         __syncthreads();
@@ -667,10 +732,10 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
                     // twiddles and spectrum from this thread's tensor-memory slot
                     const uint32_t col = ts->spec_tmem +
                                          ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
-                                         (uint32_t)(((tid >> 7) * 128) + it * ST::slot);
+                                         (uint32_t)((tid >> 7) * 128);
                     uint32_t wh[ST::head], wt[4];
-                    tc::tmem_ld<ST::head>(col, wh);
-                    tc::tmem_ld<4>(col + ST::head, wt);
+                    tc::tmem_ld<ST::head>(col + it * ST::head, wh);
+                    tc::tmem_ld<4>(col + ST::tail_col + it * 4, wt);
                     float fw[ST::words];
 #pragma unroll
                     for (int i = 0; i < ST::words; ++i)
@@ -736,15 +801,20 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             V ul[R / 2];  // factor values first: their L2 latency overlaps the pass
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) ul[q] = ur[o + q * S0];
-            V wp[R];
-            powers<R>(w0[j], wp);
             V x[R];
+            {
+                const TwPow<R, V> wp(w0[j]);
 #pragma unroll
-            for (int p = 0; p < R; ++p) {
-                const V y = buf[sidx<V>(o + p * S0)];
-                x[bitrev(p, R)] = (p == 0) ? y : cmulc(y, wp[p]);
+                for (int p = 0; p < R; ++p) x[bitrev(p, R)] = wp.mulc(buf[sidx<V>(o + p * S0)], p);
             }
             dit_halfout<R>(x);
+            if constexpr (STM) {  // this group's R accumulator words, after the butterflies
+                uint32_t aw[R];
+                tc::tmem_ld<R>(acc_col + j * R, aw);
+#pragma unroll
+                for (int q = 0; q < R / 2; ++q)
+                    acc[j][q] = mk<V>(__uint_as_float(aw[2 * q]), __uint_as_float(aw[2 * q + 1]));
+            }
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) {
                 const V uu = ul[q];
@@ -755,11 +825,31 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
                     acc[j][q].y = fma(uu.y, x[q].y, acc[j][q].y);
                 }
             }
+            if constexpr (STM) {
+                uint32_t aw[R];
+#pragma unroll
+                for (int q = 0; q < R / 2; ++q) {
+                    aw[2 * q] = __float_as_uint(acc[j][q].x);
+                    aw[2 * q + 1] = __float_as_uint(acc[j][q].y);
+                }
+                tc::tmem_st<R>(acc_col + j * R, aw);
+            }
         }
+        if constexpr (STM) tc::tmem_wait_st();
         __syncthreads();
     }
 
     // ---- epilogue: beta = D1 w (forward) / D2 w (adjoint), row 0, write once
+    if constexpr (STM) {
+        uint32_t aw[32];
+        tc::tmem_ld<32>(acc_col, aw);
+#pragma unroll
+        for (int j = 0; j < J0; ++j)
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q)
+                acc[j][q] = mk<V>(__uint_as_float(aw[2 * (j * (R / 2) + q)]),
+                                  __uint_as_float(aw[2 * (j * (R / 2) + q) + 1]));
+    }
     T g0 = T(0);
     if (P.row0 && P.adjoint && lead) g0 = in[0];
 #pragma unroll
@@ -912,9 +1002,9 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
                     wt[i - ST::head] = v;
             }
             const uint32_t col = tcs.spec_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
-                                 (uint32_t)(((tid >> 7) * 128) + it * ST::slot);
-            tc::tmem_st<ST::head>(col, wh);
-            tc::tmem_st<4>(col + ST::head, wt);
+                                 (uint32_t)((tid >> 7) * 128);
+            tc::tmem_st<ST::head>(col + it * ST::head, wh);
+            tc::tmem_st<4>(col + ST::tail_col + it * 4, wt);
         }
         tc::tmem_wait_st();
         tc::fence_before_sync();
@@ -1106,8 +1196,9 @@ int dispatch_geom(const Geometry& g, const ExecParams<T>& P, int64_t batch, cuda
     constexpr bool f32 = std::is_same<T, float>::value;
     if constexpr (I < SchedTable<f32>::size) {
         constexpr Sched e = SchedTable<f32>::at(I);
-        if (g.logLC == e.logLC && g.C == e.C && g.NT == e.NT && g.MINB == e.MINB)
-            return launch_inst<T, e.logLC, radix_for(f32, e.logLC), e.C, e.NT, e.MINB, RAGGED,
+        if (g.logLC == e.logLC && g.C == e.C && g.NT == e.NT && g.MINB == e.MINB &&
+            g.R == sched_radix(e, f32))
+            return launch_inst<T, e.logLC, sched_radix(e, f32), e.C, e.NT, e.MINB, RAGGED,
                                false>(P, batch, s);
         return dispatch_geom<T, RAGGED, I + 1>(g, P, batch, s);
     } else {
@@ -1123,8 +1214,9 @@ int dispatch_geom_tc(const Geometry& g, const ExecParams<float>& P, int64_t batc
                      cudaStream_t s) {
     if constexpr (I < SchedTableTC::size) {
         constexpr Sched e = SchedTableTC::at(I);
-        if (g.logLC == e.logLC && g.C == e.C && g.NT == e.NT && g.MINB == e.MINB)
-            return launch_inst<float, e.logLC, radix_for(true, e.logLC), e.C, e.NT, e.MINB,
+        if (g.logLC == e.logLC && g.C == e.C && g.NT == e.NT && g.MINB == e.MINB &&
+            g.R == sched_radix(e, true))
+            return launch_inst<float, e.logLC, sched_radix(e, true), e.C, e.NT, e.MINB,
                                RAGGED, true>(P, batch, s);
         return dispatch_geom_tc<RAGGED, I + 1>(g, P, batch, s);
     } else {

@@ -58,10 +58,35 @@ __device__ __forceinline__ V cwmul(V a, V b) {
     return mk<V>(a.x * b.x, a.y * b.y);
 }
 
-// x * omega_{N}^{i} (FWD) or x * omega_{N}^{-i}, omega_N = exp(-2 pi i / N), N <= 16.
+// x * omega_{N}^{i} (FWD) or x * omega_{N}^{-i}, omega_N = exp(-2 pi i / N), N <= 32.
+template <int N, int I, bool FWD, typename V>
+__device__ __forceinline__ V rot(V x);
+
+// Odd multiples of 2 pi / 32 (N = 32 only): cos and sin of pi/16 and 3 pi/16, then the
+// symmetries of the circle.
+template <int K32, bool FWD, typename V>
+__device__ __forceinline__ V rot32_odd(V x) {
+    using S = decltype(V::x);
+    constexpr S ca = S(0.98078528040323044913);  // cos(pi/16)
+    constexpr S sa = S(0.19509032201612826785);  // sin(pi/16)
+    constexpr S cb = S(0.83146961230254523708);  // cos(3 pi/16)
+    constexpr S sb = S(0.55557023301960222474);  // sin(3 pi/16)
+    // angle t = 2 pi kk / 32, kk odd; forward multiplies by (cos t, -sin t)
+    constexpr int kk = FWD ? K32 : (32 - K32) % 32;
+    constexpr S cs[32] = {S(1), ca, S(0), cb, S(0), sb, S(0), sa, S(0), -sa, S(0), -sb, S(0), -cb,
+                          S(0), -ca, S(0), -ca, S(0), -cb, S(0), -sb, S(0), -sa, S(0), sa, S(0),
+                          sb, S(0), cb, S(0), ca};
+    constexpr S sn[32] = {S(0), sa, S(0), sb, S(0), cb, S(0), ca, S(0), ca, S(0), cb, S(0), sb,
+                          S(0), sa, S(0), -sa, S(0), -sb, S(0), -cb, S(0), -ca, S(0), -ca, S(0),
+                          -cb, S(0), -sb, S(0), -sa};
+    return mk<V>(fma(x.x, cs[kk], x.y * sn[kk]), fma(x.y, cs[kk], -x.x * sn[kk]));
+}
+
 template <int N, int I, bool FWD, typename V>
 __device__ __forceinline__ V rot(V x) {
     using S = decltype(V::x);
+    static_assert(N <= 32, "rotations up to omega_32");
+    if constexpr ((I * 32 / N) % 2 == 1) return rot32_odd<(I * 32 / N) % 32, FWD>(x);
     constexpr int k = (I * 16 / N) % 16;  // angle in units of 2 pi / 16
     constexpr S c8 = S(0.70710678118654752440);
     constexpr S c1 = S(0.92387953251128675613);

@@ -5,7 +5,8 @@ against the oracle (needs a GPU).
 A schedule changes only the order of the FFT's floating-point operations, so each one must
 meet the same tolerance (max |beta - beta_ref| / ||alpha||_1: float64 1e-12, float32 5e-6).
 The lengths below put at least one plan on every schedule of the table: FFT lengths 2^8 ...
-2^18, single CTAs, clusters of 2/4/8 and the multi-pass kernels on full and half slices.
+2^18, single CTAs, clusters of 2/4/8 (radix 16 and radix 32) and the multi-pass kernels on
+full and half slices.
 """
 import numpy as np
 import pytest
@@ -70,8 +71,9 @@ def test_every_schedule(tdh, kind, n, prec):
         assert s["index"] == i and s["count"] == count, s
         assert (1 << s["logLC"]) * s["C"] == 1 << s["logL"], s
         c = compiled[i]
-        assert (c["logLC"], c["C"], c["NT"], c["MINB"]) == (s["logLC"], s["C"], s["NT"], s["MINB"])
-        seen.add((s["logLC"], s["C"], s["NT"], s["MINB"], c["multipass"]))
+        assert (c["logLC"], c["C"], c["R"], c["NT"], c["MINB"]) == \
+            (s["logLC"], s["C"], s["R"], s["NT"], s["MINB"])
+        seen.add((s["logLC"], s["C"], s["R"], s["NT"], s["MINB"], c["multipass"]))
         y = plan.execute(x)
         g = plan.adjoint(x)
         torch.cuda.synchronize()

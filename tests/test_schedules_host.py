@@ -53,13 +53,18 @@ def test_every_schedule_is_a_valid_split(tdh, prec, ragged):
     seen_any = 0
     for logL in range(8, (14 if prec == FP32 else 13) + 10):
         sched = tdh.compiled_schedules(prec, logL, ragged)
-        keys = [(s["logLC"], s["C"], s["NT"], s["MINB"], s["multipass"]) for s in sched]
+        keys = [(s["logLC"], s["C"], s["NT"], s["MINB"], s["multipass"], s["R"]) for s in sched]
         assert len(set(keys)) == len(keys), (logL, keys)
         for s in sched:
             seen_any += 1
             lc, C, R, NT = s["logLC"], s["C"], s["R"], s["NT"]
             assert lc + C.bit_length() - 1 == logL, (logL, s)
-            assert R == _radix(prec, lc)
+            if R == 32:
+                # radix-32 passes: float32 2^14-point slices of 2-8-CTA clusters, 512 threads
+                # (their accumulators live in tensor memory), the default there
+                assert prec == FP32 and lc == 14 and 2 <= C <= 8 and NT == 512, s
+            else:
+                assert R == _radix(prec, lc)
             if C > 8:
                 # 2: the cross stage moves its blocks with bulk tensor copies (16 ... 256 slices)
                 assert s["multipass"] in ((1, 2) if C <= 256 else (1,)), s
@@ -81,6 +86,18 @@ def test_every_schedule_is_a_valid_split(tdh, prec, ragged):
             assert NT * s["MINB"] <= 2048 and 65536 // (NT * s["MINB"]) >= 32
             assert LC * es + (LC // 2) * es <= SMEM_MAX  # FFT buffer and scaled input
     assert seen_any > 20
+
+
+def test_radix32_variants_are_candidates(tdh):
+    """2^15 ... 2^17 float32 points (2, 4, 8 slices of 2^14) default to the radix-32 kernel,
+    with the radix-16 one as a candidate, dense and ragged; float64 has none."""
+    for logL in (15, 16, 17):
+        for ragged in (False, True):
+            sched = tdh.compiled_schedules(FP32, logL, ragged)
+            assert (sched[0]["logLC"], sched[0]["R"]) == (14, 32), (logL, sched[0])
+            rs = [s["R"] for s in sched if s["logLC"] == 14 and s["NT"] == 512]
+            assert sorted(rs) == [16, 32], (logL, ragged, rs)
+        assert all(s["R"] != 32 for s in tdh.compiled_schedules(FP64, logL))
 
 
 def test_lengths_without_a_kernel(tdh):
