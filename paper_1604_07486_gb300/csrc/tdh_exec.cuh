@@ -544,6 +544,21 @@ __device__ __forceinline__ void middle_inv(V* buf, const V* twt, TcState* ts) {
     }
 }
 
+// Cross stage, float32: the values at the pair of positions (pos, pos+1), pos even, in each of
+// the C CTAs' buffers (one 16-byte access per CTA); a[u][j] = position pos + u of CTA j.
+template <int C, typename V>
+__device__ __forceinline__ void cross_pair_load(V* const (&rbuf)[C], int pos, V (&a)[2][C]) {
+    const bool swp = pair_swapped<V>(pos);
+    const int sp = sidx<V>(pos) & ~1;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        V e0, e1;
+        pair_load(rbuf[j] + sp, e0, e1);
+        a[0][j] = swp ? e1 : e0;
+        a[1][j] = swp ? e0 : e1;
+    }
+}
+
 // One vector: v = D alpha -> all K rank terms -> beta (the whole of Fig. 1 steps 3-5).
 template <typename T, int LOGLC, int R, int C, int NT, bool TC, bool STM>
 __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* in, T* out,
@@ -714,18 +729,28 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
                     for (int j = 0; j < C; ++j) rbuf[j][sp] = cmulc(a[j], twj[j]);
                 }
             }
+            // float32: the pair (pos, pos+1) per thread and iteration.  Up to C = 4 the next
+            // iteration's remote values are loaded before this iteration's results are stored
+            // (other positions, so the early load reads final values): one remote round trip
+            // overlaps the arithmetic.  (C = 8 has two iterations and no registers to spare.)
+            constexpr bool kAhead = kPairs && C <= 4;
+            V an[2][C];
+            if constexpr (kAhead) cross_pair_load<C>(rbuf, k1 * PPC + 2 * tid, an);
 #pragma unroll 1
             for (int pi = 2 * tid, it = 0; kPairs && pi < PPC; pi += 2 * NT, ++it) {
                 const int pos = k1 * PPC + pi;  // even: the pair (pos, pos+1) is contiguous
                 const bool swp = pair_swapped<V>(pos);
                 const int sp = sidx<V>(pos) & ~1;
                 V a[2][C], sc[2][C], tw[2];
+                if constexpr (kAhead) {
 #pragma unroll
-                for (int j = 0; j < C; ++j) {
-                    V e0, e1;
-                    pair_load(rbuf[j] + sp, e0, e1);
-                    a[0][j] = swp ? e1 : e0;
-                    a[1][j] = swp ? e0 : e1;
+                    for (int j = 0; j < C; ++j) {
+                        a[0][j] = an[0][j];
+                        a[1][j] = an[1][j];
+                    }
+                    if (pi + 2 * NT < PPC) cross_pair_load<C>(rbuf, pos + 2 * NT, an);
+                } else {
+                    cross_pair_load<C>(rbuf, pos, a);
                 }
                 using ST = SpecTmem<T, LOGLC, C, NT, 1, false>;
                 if constexpr (STM) {
