@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "tdh_internal.cuh"
 
@@ -321,9 +322,25 @@ int run_host(tdh_plan_t plan, const void* h_in, void* h_out, int64_t batch, void
     }
     int64_t chunk = std::max<int64_t>((int64_t)((8u << 20) / vec_bytes), (batch + 3) / 4);
     chunk = std::max<int64_t>(1, std::min(chunk, batch));
-    const int64_t nchunks = (batch + chunk - 1) / chunk;
+    // Chunk sizes.  Each chunk's conversion has a fixed cost (a launch, its prologue and tail),
+    // so chunks stay few; from three chunks' worth of vectors on, the first and the last are a
+    // quarter chunk (a short copy in before the first conversion, a short copy out after the
+    // last) around two equal middle chunks of up to two chunks each.
+    std::vector<int64_t> sizes;
+    if (batch >= 3 * chunk) {
+        const int64_t e = std::max<int64_t>(1, chunk / 4), rem = batch - 2 * e;
+        const int64_t nmid = (rem + 2 * chunk - 1) / (2 * chunk);
+        sizes.push_back(e);
+        for (int64_t j = 0; j < nmid; ++j) sizes.push_back(rem * (j + 1) / nmid - rem * j / nmid);
+        sizes.push_back(e);
+    } else {
+        for (int64_t rem = batch; rem > 0; rem -= std::min(chunk, rem))
+            sizes.push_back(std::min(chunk, rem));
+    }
+    const int64_t slot_vecs = *std::max_element(sizes.begin(), sizes.end());
+    const int64_t nchunks = (int64_t)sizes.size();
     const int nslots = nchunks > 1 ? 2 : 1;
-    const size_t slot_bytes = (vec_bytes * (size_t)chunk + 255) / 256 * 256;  // aligned slots
+    const size_t slot_bytes = (vec_bytes * (size_t)slot_vecs + 255) / 256 * 256;  // aligned
     std::lock_guard<std::mutex> lock(plan->host_mu);
     cudaStream_t s = as_stream(stream);
     cudaStream_t cin = plan->hs[0], cout = plan->hs[1];
@@ -338,14 +355,15 @@ int run_host(tdh_plan_t plan, const void* h_in, void* h_out, int64_t batch, void
     cudaError_t e = cudaEventRecord(hev[0], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, hev[0], 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, hev[0], 0);
-    for (int64_t i = 0; e == cudaSuccess && rc == TDH_OK && i < nchunks; ++i) {
+    int64_t first = 0;  // index of the chunk's first vector
+    for (int64_t i = 0; e == cudaSuccess && rc == TDH_OK && i < nchunks; first += sizes[i++]) {
         const int sl = (int)(i % nslots);
-        const int64_t nb = std::min(chunk, batch - i * chunk);
+        const int64_t nb = sizes[i];
         const size_t bytes = vec_bytes * (size_t)nb;
         // copy in once the conversion of the chunk that last used this slot has read it
         if (i >= nslots) e = cudaStreamWaitEvent(cin, hev[3 + sl], 0);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(din(i), hi + vec_bytes * (size_t)(i * chunk), bytes,
+            e = cudaMemcpyAsync(din(i), hi + vec_bytes * (size_t)first, bytes,
                                 cudaMemcpyHostToDevice, cin);
         if (e == cudaSuccess) e = cudaEventRecord(hev[1 + sl], cin);
         // convert once the chunk is in and the slot's previous result has been copied out
@@ -358,7 +376,7 @@ int run_host(tdh_plan_t plan, const void* h_in, void* h_out, int64_t batch, void
         // copy out once converted
         if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, hev[3 + sl], 0);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ho + vec_bytes * (size_t)(i * chunk), dout(i), bytes,
+            e = cudaMemcpyAsync(ho + vec_bytes * (size_t)first, dout(i), bytes,
                                 cudaMemcpyDeviceToHost, cout);
         if (e == cudaSuccess) e = cudaEventRecord(hev[5 + sl], cout);
     }
