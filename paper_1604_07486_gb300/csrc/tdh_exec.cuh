@@ -559,6 +559,23 @@ __device__ __forceinline__ void cross_pair_load(V* const (&rbuf)[C], int pos, V 
     }
 }
 
+// The inverse middle passes np-2 ... 1 with a barrier between passes but none after the last:
+// the caller issues loads that do not touch the FFT buffer before that barrier.
+template <int I, int LOGLC, int R, int NT, bool TC, typename V>
+__device__ __forceinline__ void middle_inv_open(V* buf, const V* twt, TcState* ts) {
+    constexpr PassGeom G{LOGLC, R};
+    if constexpr (I >= 1) {
+        if constexpr (TC)
+            tc_pass<G.rad(I), G.M(I), G.S(I), G.LC(), NT, false>(buf, twt + G.twoff(I), *ts);
+        else
+            pass_inv<G.rad(I), G.M(I), G.S(I), G.LC(), NT>(buf, twt + G.twoff(I));
+        if constexpr (I > 1) {
+            __syncthreads();
+            middle_inv_open<I - 1, LOGLC, R, NT, TC>(buf, twt, ts);
+        }
+    }
+}
+
 // One vector: v = D alpha -> all K rank terms -> beta (the whole of Fig. 1 steps 3-5).
 template <typename T, int LOGLC, int R, int C, int NT, bool TC, bool STM>
 __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* in, T* out,
@@ -626,6 +643,22 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 #pragma unroll
             for (int q = 0; q < R / 2; ++q) acc[j][q] = mk<V>(0, 0);
     }
+    // The factor values of both passes 0 are read from L2 once per rank term.  In the float32
+    // kernels they are loaded ahead, before the barrier that precedes their use, so their
+    // latency overlaps the wait: ul0 (forward pass 0, every group) at the end of the previous
+    // rank term, ulp (inverse pass 0, the first group) before the last inverse middle pass's
+    // barrier.  (Measured: 0.5 % faster there; float64 and tensor-core kernels, which have no
+    // registers to spare, load them at the start of the pass.)
+    constexpr bool kAhead = !TC && sizeof(T) == 4;
+    V ul0[J0][R / 2], ulp[R / 2];
+    auto load_ul0 = [&](int64_t r) {
+        const V* u = P.u + ((int64_t)r * C + k1) * P.u_stride;
+#pragma unroll
+        for (int j = 0; j < J0; ++j)
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) ul0[j][q] = u[tid + j * NT + q * S0];
+    };
+    if (kAhead && r_begin < r_end) load_ul0(r_begin);
     __syncthreads();
 
     V* rbuf[C];
@@ -642,11 +675,7 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
         const V* ur = P.u + ((int64_t)r * C + k1) * P.u_stride;
         const T cpair = (P.full && P.pair_c) ? P.pair_c[r] : T(1);
         // ---- forward pass 0: inputs u_r o v (upper half zero), radix R, stride S0
-        V ul0[J0][R / 2];  // the factor values of every group first: one L2 latency
-#pragma unroll
-        for (int j = 0; j < J0; ++j)
-#pragma unroll
-            for (int q = 0; q < R / 2; ++q) ul0[j][q] = ur[tid + j * NT + q * S0];
+        if constexpr (!kAhead) load_ul0(r);
 #pragma unroll
         for (int j = 0; j < J0; ++j) {
             const int o = tid + j * NT;
@@ -680,7 +709,6 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 #pragma unroll
                 for (int q = 0; q < RL; ++q) buf[sidx<V>(g * RL + q)] = x[q];
             }
-            __syncthreads();
         } else {
             // Last local pass (radix RL, stride 1), then the cross-CTA stage, then the first
             // inverse local pass.  In the cross stage each thread takes two consecutive
@@ -816,16 +844,23 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
 #pragma unroll
                 for (int q = 0; q < RL; ++q) buf[sidx<V>(g * RL + q)] = x[q];
             }
-            __syncthreads();
         }
-        middle_inv<G.np() - 2, LOGLC, R, NT, TC>(buf, twt, ts);
+        if constexpr (G.np() >= 3) {
+            __syncthreads();
+            middle_inv_open<G.np() - 2, LOGLC, R, NT, TC>(buf, twt, ts);
+        }
+        if constexpr (kAhead) {
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) ulp[q] = ur[tid + q * S0];
+        }
+        __syncthreads();
         // ---- inverse pass 0: outputs [0, LC/2) only, accumulate u_r o y
 #pragma unroll
         for (int j = 0; j < J0; ++j) {
             const int o = tid + j * NT;
-            V ul[R / 2];  // factor values first: their L2 latency overlaps the pass
+            V ul[R / 2];  // factor values before the pass: their L2 latency overlaps it
 #pragma unroll
-            for (int q = 0; q < R / 2; ++q) ul[q] = ur[o + q * S0];
+            for (int q = 0; q < R / 2; ++q) ul[q] = (kAhead && j == 0) ? ulp[q] : ur[o + q * S0];
             V x[R];
             {
                 const TwPow<R, V> wp(w0[j]);
@@ -861,6 +896,9 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
             }
         }
         if constexpr (STM) tc::tmem_wait_st();
+        // unconditional (the last rank term reloads its own values): a conditional load would
+        // keep ul0 live across the whole loop body
+        if constexpr (kAhead) load_ul0(r + 1 < r_end ? r + 1 : r);
         __syncthreads();
     }
 
