@@ -42,9 +42,9 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
     }
     if (g->C > 512) return false;  // C > 8: multi-pass through global memory
     g->R = radix_for(prec != TDH_FP64, g->logLC);
-    // float32 2^14-point slices of 2-8-CTA clusters: radix 32, 32, 16 (three shared-memory
-    // passes instead of four; their accumulators are in tensor memory)
-    if (prec == TDH_FP32 && g->logLC == 14 && g->C >= 2 && g->C <= 8) g->R = 32;
+    // float32 2^14-point slices, one CTA or 2-8-CTA clusters: radix 32, 32, 16 (three
+    // shared-memory passes instead of four; their accumulators are in tensor memory)
+    if (prec == TDH_FP32 && g->logLC == 14 && g->C <= 8) g->R = 32;
     g->NT = std::min(512, (1 << g->logLC) / g->R);
     g->MINB = 1;
     if (g->C > 8) mp_threads(prec, g->logLC, &g->NT, &g->MINB);

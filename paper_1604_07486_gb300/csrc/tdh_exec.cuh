@@ -94,7 +94,7 @@ constexpr Sched kSchedF32[] = {
     {14, 1, 512, 1},  {14, 2, 512, 1},  {14, 4, 512, 1},  {14, 8, 512, 1},  {13, 2, 256, 2},
     {13, 4, 256, 2},  {13, 8, 256, 2},  {9, 2, 64, 1},    {8, 4, 32, 1},    {10, 2, 64, 1},
     {11, 2, 128, 1},  {12, 2, 256, 2},  {14, 2, 512, 1, 32}, {14, 4, 512, 1, 32},
-    {14, 8, 512, 1, 32},
+    {14, 8, 512, 1, 32}, {14, 1, 512, 1, 32}, {13, 1, 256, 2, 32},
 };
 constexpr Sched kSchedF64[] = {
     {8, 1, 32, 1},    {8, 1, 32, 16},   {9, 1, 64, 1},    {9, 1, 64, 8},    {10, 1, 128, 1},
@@ -138,25 +138,38 @@ __host__ __device__ constexpr int tc_cols(int LOGLC, int R, int NT) {
     return c;
 }
 
-// Float32 cluster kernels with one 512-thread CTA per SM (local FFT 2^14) keep in tensor
-// memory, which they do not otherwise use: the cross stage's spectrum and twiddles -- the same
-// for every rank term and every vector -- instead of reading them from L2 for every rank term,
-// and the output accumulators w, which otherwise hold 32 registers across the whole rank loop.
-// Each thread owns one TMEM lane (thread t of warp w: lane 32 (w % 4) + t); the four warps
-// that share a lane set take 128 columns each: per cross-stage iteration the first `head` of
-// its 4 + 4C words (two twiddles, the spectrum of two positions) at columns [0, 64), the last 4
-// at [64, 96), the 32 accumulator words at [96, 128).
+// Float32 kernels whose local FFT has 32 points per thread (2^14 points on 512 threads, or
+// single-CTA FFTs of 2^13 points on 256 threads, two CTAs per SM) keep in tensor memory,
+// which they do not otherwise use: the spectrum values their threads multiply by -- the same
+// for every rank term and every vector -- instead of reading them from L2 for every rank
+// term, and the output accumulators w, which otherwise hold 32 registers across the whole
+// rank loop (the room radix-32 passes need).  Each thread owns one TMEM lane (thread t of
+// warp w: lane 32 (w % 4) + t); the four warps that share a lane set take 128 columns each.
+//   cluster kernels (C = 2, 4, 8; 512 threads): per cross-stage iteration the first `head` of
+//     its 4 + 4C words (two twiddles, the spectrum of two positions) at columns [0, 64), the
+//     last 4 at [64, 96);
+//   single-CTA kernels: the spectrum of each of the thread's last-pass groups, in the order
+//     the group multiplies by it, at columns [0, 64);
+//   both: the 32 accumulator words at [96, 128).
+// A CTA allocates 128 columns per 128 threads; single-CTA 2^13 kernels take more than a third
+// of an SM's shared memory, so at most two share an SM's 512 columns.
 template <typename T, int LOGLC, int C, int NT, int MINB, bool TC>
 struct SpecTmem {
-    static constexpr bool on = !TC && std::is_same<T, float>::value && C > 1 && C <= 8 &&
-                               LOGLC == 14 && NT == 512 && MINB == 1;
+    static constexpr bool f32 = !TC && std::is_same<T, float>::value;
+    static constexpr bool cluster = f32 && C > 1 && C <= 8 && LOGLC == 14 && NT == 512 &&
+                                    MINB == 1;
+    static constexpr bool single = f32 && C == 1 && ((LOGLC == 14 && NT == 512 && MINB == 1) ||
+                                                     (LOGLC == 13 && NT == 256 && MINB == 2));
+    static constexpr bool on = cluster || single;
+    static constexpr int cols = NT;                            // columns allocated
     static constexpr int iters = (1 << LOGLC) / C / (2 * NT);  // cross-stage iterations
     static constexpr int words = 4 + 4 * C;                    // per iteration
     static constexpr int head = words >= 32 ? 32 : (words >= 16 ? 16 : 8);  // first load width
     static constexpr int tail_col = 64;                        // columns of the last 4 words
     static constexpr int acc_col = 96;                         // the accumulators' 32 words
-    static_assert(!on || (words - head == 4 && iters * head == 64 && iters * 4 <= 32),
+    static_assert(!cluster || (words - head == 4 && iters * head == 64 && iters * 4 <= 32),
                   "slot layout");
+    static_assert(!single || 2 * (1 << LOGLC) / NT == 64, "single-CTA spectrum: 64 words");
 };
 
 template <typename T>
@@ -695,16 +708,27 @@ __device__ __forceinline__ void convert_vector(const ExecParams<T>& P, const T* 
         // ---- last pass (stride 1), spectrum, first inverse pass
         if constexpr (C == 1) {
 #pragma unroll 1
-            for (int g = tid; g < LC / RL; g += NT) {
+            for (int g = tid, i = 0; g < LC / RL; g += NT, ++i) {
                 V x[RL];
 #pragma unroll
                 for (int q = 0; q < RL; ++q) x[q] = buf[sidx<V>(g * RL + q)];
                 dif<RL>(x);
+                V sp[RL];
+                if constexpr (STM) {  // this group's spectrum from the thread's TMEM lane
+                    uint32_t sw[2 * RL];
+                    tc::tmem_ld<2 * RL>(ts->spec_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
+                                            (uint32_t)((tid >> 7) * 128 + i * 2 * RL),
+                                        sw);
 #pragma unroll
-                for (int jj = 0; jj < RL; ++jj) {
-                    const V s = P.spec[g * RL + bitrev(jj, RL)];
-                    x[jj] = P.adjoint ? cmulc(x[jj], s) : cmul(x[jj], s);
+                    for (int jj = 0; jj < RL; ++jj)
+                        sp[jj] = mk<V>(__uint_as_float(sw[2 * jj]), __uint_as_float(sw[2 * jj + 1]));
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < RL; ++jj) sp[jj] = P.spec[g * RL + bitrev(jj, RL)];
                 }
+#pragma unroll
+                for (int jj = 0; jj < RL; ++jj)
+                    x[jj] = P.adjoint ? cmulc(x[jj], sp[jj]) : cmul(x[jj], sp[jj]);
                 dit<RL>(x);
 #pragma unroll
                 for (int q = 0; q < RL; ++q) buf[sidx<V>(g * RL + q)] = x[q];
@@ -982,6 +1006,9 @@ __host__ __device__ constexpr size_t exec_smem_base(int LOGLC, int R) {
 }
 __host__ __device__ constexpr size_t tc_dft_bytes(int R) { return (size_t)4 * (2 * R) * (2 * R) * 2; }
 
+template <typename V, int LOGLC, int R, int NT, bool TC>
+constexpr size_t exec_smem();
+
 template <typename T, int LOGLC, int R, int C, int NT, int MINB, bool RAGGED, bool TC>
 __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
     using V = typename cx<T>::t;
@@ -1035,22 +1062,47 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
         tcs.status = P.status;
         tcs.stall = P.tc_stall;
     }
-    // float32 cluster kernels: the cross stage's twiddles and spectrum into tensor memory, once
+    // float32 kernels with 32 points per thread: the spectrum values (and the cross stage's
+    // twiddles) into tensor memory, once
     constexpr bool STM = SpecTmem<T, LOGLC, C, NT, MINB, TC>::on;
     __shared__ uint32_t stm_slot;
     if constexpr (STM) {
         using ST = SpecTmem<T, LOGLC, C, NT, MINB, TC>;
+        static_assert(ST::cols == 512 || 3 * (exec_smem<V, LOGLC, R, NT, TC>() + 1024) > 233472,
+                      "at most two CTAs of 256 columns per SM");
         constexpr int PPC = LC / C;
         if (tid < 32) {
-            tc::tmem_alloc(tc::smem_u32(&stm_slot), 512);
+            tc::tmem_alloc(tc::smem_u32(&stm_slot), ST::cols);
             tc::tmem_relinquish();
         }
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
         tcs.spec_tmem = stm_slot;
+        const uint32_t col = tcs.spec_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
+                             (uint32_t)((tid >> 7) * 128);
+        if constexpr (ST::single) {
+            // group i of the thread (g = tid + i NT) multiplies its point jj by
+            // spec[g RL + bitrev(jj)]: words [2 (i RL + jj), +1]
+            constexpr int RL = PassGeom{LOGLC, R}.rad(PassGeom{LOGLC, R}.np() - 1);
+            constexpr int NG = LC / RL / NT;
+            static_assert(NG * RL * 2 == 64, "64 spectrum words per thread");
 #pragma unroll 1
-        for (int it = 0; it < ST::iters; ++it) {
+            for (int h = 0; h < 2; ++h) {  // two halves of 32 words
+                uint32_t w[32];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int e = h * 16 + k;  // entry i RL + jj of the thread
+                    const int i = e / RL, jj = e % RL;
+                    const V v = P.spec[(tid + i * NT) * RL + bitrev(jj, RL)];
+                    w[2 * k] = __float_as_uint(v.x);
+                    w[2 * k + 1] = __float_as_uint(v.y);
+                }
+                tc::tmem_st<32>(col + h * 32, w);
+            }
+        }
+#pragma unroll 1
+        for (int it = 0; ST::cluster && it < ST::iters; ++it) {
             const int pos = k1 * PPC + 2 * tid + it * 2 * NT;
             // slot words: twiddles of the two positions, then their spectra [u][f]
             const float* tf = reinterpret_cast<const float*>(P.twx + pos);
@@ -1064,8 +1116,6 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
                 else
                     wt[i - ST::head] = v;
             }
-            const uint32_t col = tcs.spec_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) +
-                                 (uint32_t)((tid >> 7) * 128);
             tc::tmem_st<ST::head>(col + it * ST::head, wh);
             tc::tmem_st<4>(col + ST::tail_col + it * 4, wt);
         }
@@ -1128,7 +1178,7 @@ __global__ void __launch_bounds__(NT, MINB) exec_kernel(const ExecParams<T> P) {
         __syncthreads();
         if (tid < 32) {
             tc::fence_after_sync();
-            tc::tmem_dealloc(tcs.spec_tmem, 512);
+            tc::tmem_dealloc(tcs.spec_tmem, SpecTmem<T, LOGLC, C, NT, MINB, TC>::cols);
         }
     }
 }

@@ -60,9 +60,12 @@ def test_every_schedule_is_a_valid_split(tdh, prec, ragged):
             lc, C, R, NT = s["logLC"], s["C"], s["R"], s["NT"]
             assert lc + C.bit_length() - 1 == logL, (logL, s)
             if R == 32:
-                # radix-32 passes: float32 2^14-point slices of 2-8-CTA clusters, 512 threads
-                # (their accumulators live in tensor memory), the default there
-                assert prec == FP32 and lc == 14 and 2 <= C <= 8 and NT == 512, s
+                # radix-32 passes (their accumulators live in tensor memory): float32 2^14-point
+                # slices on 512 threads, one CTA or 2-8-CTA clusters, and single-CTA 2^13-point
+                # FFTs on 256 threads, two CTAs per SM
+                assert prec == FP32, s
+                assert (lc == 14 and C <= 8 and NT == 512 and s["MINB"] == 1) or \
+                    (lc == 13 and C == 1 and NT == 256 and s["MINB"] == 2), s
             else:
                 assert R == _radix(prec, lc)
             if C > 8:
@@ -89,15 +92,20 @@ def test_every_schedule_is_a_valid_split(tdh, prec, ragged):
 
 
 def test_radix32_variants_are_candidates(tdh):
-    """2^15 ... 2^17 float32 points (2, 4, 8 slices of 2^14) default to the radix-32 kernel,
-    with the radix-16 one as a candidate, dense and ragged; float64 has none."""
-    for logL in (15, 16, 17):
+    """2^14 ... 2^17 float32 points (1, 2, 4, 8 slices of 2^14) default to the radix-32
+    kernel, with the radix-16 one as a candidate, dense and ragged; float64 has none;
+    single-CTA 2^13-point FFTs have a radix-32 candidate."""
+    for logL in (14, 15, 16, 17):
         for ragged in (False, True):
             sched = tdh.compiled_schedules(FP32, logL, ragged)
             assert (sched[0]["logLC"], sched[0]["R"]) == (14, 32), (logL, sched[0])
             rs = [s["R"] for s in sched if s["logLC"] == 14 and s["NT"] == 512]
             assert sorted(rs) == [16, 32], (logL, ragged, rs)
         assert all(s["R"] != 32 for s in tdh.compiled_schedules(FP64, logL))
+    # single-CTA FFTs of 2^13 and 2^14 points have radix-32 candidates too
+    for logL, nt in ((13, 256), (14, 512)):
+        assert any(s["R"] == 32 and s["C"] == 1 and s["NT"] == nt
+                   for s in tdh.compiled_schedules(FP32, logL)), logL
 
 
 def test_lengths_without_a_kernel(tdh):
