@@ -45,6 +45,8 @@ bool choose_geometry(int prec, int logL, Geometry* g) {
     // float32 2^14-point slices, one CTA or 2-8-CTA clusters: radix 32, 32, 16 (three
     // shared-memory passes instead of four; their accumulators are in tensor memory)
     if (prec == TDH_FP32 && g->logLC == 14 && g->C <= 8) g->R = 32;
+    // the float32 multi-pass kernels (also under split-bfloat16 plans): radix 32 as well
+    if (prec != TDH_FP64 && g->C > 8) g->R = 32;
     g->NT = std::min(512, (1 << g->logLC) / g->R);
     g->MINB = 1;
     if (g->C > 8) mp_threads(prec, g->logLC, &g->NT, &g->MINB);
@@ -102,6 +104,13 @@ std::vector<Geometry> schedule_candidates(int prec, int logL, bool ragged) {
             int NT, MINB;
             mp_threads(prec, lc, &NT, &MINB);
             add(lc, 1 << (logL - lc), NT, MINB, 1);
+        }
+        // float32: the multi-pass kernels with radix-32 local passes
+        for (int lc = cap; f32 && lc >= cap - 1; --lc) {
+            if (logL - lc < 4 || logL - lc > 9) continue;
+            int NT, MINB;
+            mp_threads(prec, lc, &NT, &MINB);
+            add(lc, 1 << (logL - lc), NT, MINB, 0, 32);
         }
     }
     if (ragged) {

@@ -169,12 +169,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_fwd(const MPParams<T
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) x[q] = zl[j][q];
         dif_halfzero<R>(x);
-        V wp[R];
-        powers<R>(P.tw0[o], wp);
+        const TwPow<R, V> wp(P.tw0[o]);
 #pragma unroll
         for (int jj = 0; jj < R; ++jj) {
             const int p = bitrev(jj, R);
-            buf[sidx<V>(o + p * S0)] = (p == 0) ? x[jj] : cmul(x[jj], wp[p]);
+            buf[sidx<V>(o + p * S0)] = wp.mul(x[jj], p);
         }
     }
     __syncthreads();
@@ -252,21 +251,26 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) mp_inv(const MPParams<T
 #pragma unroll
     for (int j = 0; j < J0; ++j) {
         const int o = tid + j * NT;
-        V ul[R / 2], wl[R / 2];  // global loads first: their latency overlaps the pass
+        // global loads first: their latency overlaps the pass (radix 32, whose 64 registers
+        // of data leave no room for both, loads the accumulators after the butterflies)
+        constexpr bool kEarlyW = R <= 16;
+        V ul[R / 2], wl[R / 2];
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) {
             ul[q] = ur[o + q * S0];
-            wl[q] = w[o + q * S0];
+            if (kEarlyW) wl[q] = w[o + q * S0];
         }
-        V wp[R];
-        powers<R>(P.tw0[o], wp);
         V x[R];
+        {
+            const TwPow<R, V> wp(P.tw0[o]);
 #pragma unroll
-        for (int p = 0; p < R; ++p) {
-            const V yy = buf[sidx<V>(o + p * S0)];
-            x[bitrev(p, R)] = (p == 0) ? yy : cmulc(yy, wp[p]);
+            for (int p = 0; p < R; ++p) x[bitrev(p, R)] = wp.mulc(buf[sidx<V>(o + p * S0)], p);
         }
         dit_halfout<R>(x);
+        if constexpr (!kEarlyW) {
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) wl[q] = w[o + q * S0];
+        }
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) {
             const V uu = ul[q];
@@ -861,9 +865,14 @@ int mp_launch(const Step& st, int prec, const void* in, void* out, int64_t batch
         return TDH_ERR_UNSUPPORTED;
     }
     // slices one below the shared-memory cap run two CTAs per SM; longer FFTs keep full slices
-    if (prec != TDH_FP64)
-        return st.ex.g.logLC == 13 ? run_typed<float, 13, 16, 256>(st, in, out, batch, adjoint, s)
-                                   : run_typed<float, 14, 16, 512>(st, in, out, batch, adjoint, s);
+    if (prec != TDH_FP64) {
+        const bool r32 = st.ex.g.R == 32;
+        if (st.ex.g.logLC == 13)
+            return r32 ? run_typed<float, 13, 32, 256>(st, in, out, batch, adjoint, s)
+                       : run_typed<float, 13, 16, 256>(st, in, out, batch, adjoint, s);
+        return r32 ? run_typed<float, 14, 32, 512>(st, in, out, batch, adjoint, s)
+                   : run_typed<float, 14, 16, 512>(st, in, out, batch, adjoint, s);
+    }
     return st.ex.g.logLC == 12 ? run_typed<double, 12, 8, 256>(st, in, out, batch, adjoint, s)
                                : run_typed<double, 13, 8, 512>(st, in, out, batch, adjoint, s);
 }

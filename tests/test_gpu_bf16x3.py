@@ -66,7 +66,7 @@ def test_every_tensor_core_schedule(tdh, n):
     for i in range(count):
         plan.set_schedule(i)
         s = plan.schedules()[0]
-        seen.add((s["logLC"], s["C"], s["NT"], s["MINB"], compiled[i]["multipass"]))
+        seen.add((s["logLC"], s["C"], s["R"], s["NT"], s["MINB"], compiled[i]["multipass"]))
         y = plan.execute(x)
         g = plan.adjoint(x)
         torch.cuda.synchronize()

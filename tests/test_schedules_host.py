@@ -45,6 +45,8 @@ def test_default_schedule_rule(tdh, prec):
         else:
             assert (d["logLC"], d["C"], d["multipass"]) == (cap, 1 << (logL - cap), 1)
         assert d["MINB"] == (2 if d["multipass"] and d["logLC"] == cap - 1 else 1)
+        if d["multipass"]:  # float32 multi-pass slices default to radix 32
+            assert d["R"] == (32 if prec == FP32 else 8), d
 
 
 @pytest.mark.parametrize("ragged", [False, True])
@@ -60,12 +62,14 @@ def test_every_schedule_is_a_valid_split(tdh, prec, ragged):
             lc, C, R, NT = s["logLC"], s["C"], s["R"], s["NT"]
             assert lc + C.bit_length() - 1 == logL, (logL, s)
             if R == 32:
-                # radix-32 passes (their accumulators live in tensor memory): float32 2^14-point
-                # slices on 512 threads, one CTA or 2-8-CTA clusters, and single-CTA 2^13-point
-                # FFTs on 256 threads, two CTAs per SM
+                # radix-32 passes, float32 only: 2^14-point slices on 512 threads, one CTA or
+                # 2-8-CTA clusters, and single-CTA 2^13-point FFTs on 256 threads, two CTAs per
+                # SM (their accumulators live in tensor memory); the multi-pass kernels' slices
+                # (plain cross stage)
                 assert prec == FP32, s
                 assert (lc == 14 and C <= 8 and NT == 512 and s["MINB"] == 1) or \
-                    (lc == 13 and C == 1 and NT == 256 and s["MINB"] == 2), s
+                    (lc == 13 and C == 1 and NT == 256 and s["MINB"] == 2) or \
+                    (C > 8 and s["multipass"] == 1), s
             else:
                 assert R == _radix(prec, lc)
             if C > 8:
