@@ -72,12 +72,16 @@ def tune(plan, batch, args):
     return ms, desc
 
 
-def flops_per_vector(K, L):
-    """Algorithmic flops of one vector: per rank term a forward and an inverse complex FFT of
-    L points (5 L log2 L each), the spectrum multiply (6 L), and the scalings on the way in
-    and out (2 and 4 flops per packed point, L/2 points each)."""
+def flops_per_vector(K, n):
+    """Algorithmic flops of one vector of n coefficients, the path's per-unit figure: per rank
+    term two real FFTs of length L = nextpow2(2n - 1) (2.5 L log2 L each, 10 n log2 L for the
+    pair) plus 9 flops per coefficient of pointwise work (factor and spectrum products,
+    scalings), i.e. K (10 log2 L + 9) per coefficient.  The kernels compute the same transform
+    with packed complex FFTs (even/odd or rank-pair packing); that is not counted as less
+    work."""
     import math
-    return K * (10 * L * math.log2(L) + 6 * L + 3 * L)
+    L = 1 << max(0, math.ceil(math.log2(max(2 * n - 1, 1))))
+    return K * n * (10 * math.log2(L) + 9)
 
 
 class ClockSampler:
@@ -495,8 +499,7 @@ def main():
     value, total_ms = job_throughput(sum(step_ms), coeffs_per_step, args.steps, world, dist)
 
     # roofline of the execute kernel (the only kernel in the timed region)
-    L = N  # parity-packed correlation of n/2 complex points, padded to n
-    flops = sum(flops_per_vector(plans32[k].K, L) * BATCH for k in KINDS) * args.steps
+    flops = sum(flops_per_vector(plans32[k].K, N) * BATCH for k in KINDS) * args.steps
     achieved = flops / (total_ms / 1e3) / 1e12
     clocks = sampler.summary()
     peaks = measured_peaks()
@@ -536,7 +539,7 @@ def main():
         if rank == 0:
             for k in KINDS:
                 err64[k] = oracle_error(alpha, y64[k].cpu().numpy(), k, [0, BATCH - 1], rows)
-        flops64 = sum(flops_per_vector(plans64[k].K, L) * BATCH for k in KINDS)
+        flops64 = sum(flops_per_vector(plans64[k].K, N) * BATCH for k in KINDS)
         fp64 = {"value": world * coeffs_per_step * reps / (ms64 / 1e3), "unit": "coeffs/s",
                 "ms_per_step": ms64 / reps, "reps": reps, "K": {k: plans64[k].K for k in KINDS},
                 "plans": PLAN64, "error_vs_oracle": err64, "schedule": tuned64,
@@ -651,7 +654,7 @@ def run_extra(args, rank, world, local):
         y = torch.empty_like(x)
         fn = lambda: plan.execute(x, out=y)
         coeffs, dtype = n * B, "f64"
-        flops = flops_per_vector(plan.K, 1024) * B
+        flops = flops_per_vector(plan.K, n) * B
         bound, peak, unit, pnote = "alu", apeaks["fp64"], "TFLOP/s", "FP64 DFMA " + apeaks["note"]
         config = {"workload": "leg2cheb n=1024 batch=1 fp64 tol=1e-15", "K": plan.K}
         check = lambda: {"leg2cheb": float(np.abs(y.cpu().numpy() - oracle.matvec(oracle.LEG2CHEB, None, alpha)).max() / np.abs(alpha).sum())}
@@ -679,8 +682,7 @@ def run_extra(args, rank, world, local):
         graph_launches = tdh.launch_count() - c0  # kernels in the captured graph
         fn = graph.replay
         coeffs, dtype = int(offs[-1]), "f32"
-        Ls = [max(256, 1 << int(math.ceil(math.log2(max(2 * ((int(n) + 1) // 2) - 1, 1))))) for n in lengths]
-        flops = sum(flops_per_vector(plan.K, L) for L in Ls)
+        flops = sum(flops_per_vector(plan.K, int(n)) for n in lengths)
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA " + apeaks["note"]
         config = {"workload": "ragged leg2cheb 4096 vectors, degrees log-uniform [64, 65536), fp32, one CUDA-graph launch",
                   "K": plan.K, "plan": PLAN32["leg2cheb"], "coefficients": coeffs}
@@ -717,8 +719,8 @@ def run_extra(args, rank, world, local):
             ev_mid.append(e)
             pu.execute(x, out=yu)
         coeffs, dtype = 2 * n * B, "f32"
-        # both Jacobi steps: rank pairs packed, FFT length 2^21 (factor count from the plan)
-        flops = 2 * flops_per_vector(pj.K, 1 << 21) / 2 * B
+        # both Jacobi steps (factor count from the plan)
+        flops = 2 * flops_per_vector(pj.K, n) * B
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA " + apeaks["note"] + " (Jacobi multi-pass part)"
         config = {"workload": "jacobi (0.1,-0.3)->(0,0) + ultraspherical 0.25->1.25, n=2^20, batch=16, fp32 execute, fp64 plan, tol 1e-13",
                   "K_jacobi_max_step": pj.K}
@@ -758,7 +760,7 @@ def run_extra(args, rank, world, local):
             beta = convert(x, plan)
             (wgt * beta * beta).sum().backward()
         coeffs, dtype = n * B, "f32"
-        flops = 2 * flops_per_vector(plan.K, 8192) * B
+        flops = 2 * flops_per_vector(plan.K, n) * B
         bound, peak, unit, pnote = "alu", fp32_peak, "TFLOP/s", "FP32 FFMA " + apeaks["note"]
         config = {"workload": "autograd leg2cheb n=8192 batch=1024 fp32: forward + loss + backward (adjoint kernel)",
                   "K": plan.K, "plan": PLAN32["leg2cheb"]}
