@@ -190,6 +190,26 @@ int tdh_plan_execute_host(tdh_plan_t plan, const void* in, void* out, int64_t ba
                           void* stream);
 
 /*
+ * tdh_plan_execute_ragged_host -- tdh_plan_execute_ragged for vectors in HOST memory: vector v
+ * occupies in[offsets[v] .. offsets[v+1]) and its result the same range of out.  in, out:
+ * host arrays of the plan's precision (page-locked memory lets the copies overlap the work);
+ * offsets: HOST, batch + 1 int64.  Because the offsets are on the host, every length is checked
+ * before anything is enqueued: offsets[0] < 0, a decreasing offset or a vector longer than
+ * n_max is TDH_ERR_INVALID_ARG; overlapping in and out ranges are TDH_ERR_ALIAS.  From 24 MB
+ * of coefficients on, the batch moves through the device in chunks of whole vectors (about
+ * a sixteenth of the coefficients first and last, the rest in two halves): the copy of one
+ * chunk in, the conversion of the previous one (the device ragged path) and the copy of the
+ * one before out overlap on the plan's copy streams and `stream`.  Results equal those of
+ * tdh_plan_execute_ragged bit for bit (each vector is converted the same way in any chunk).
+ * The plan requirements are those of tdh_plan_execute_ragged.  Device staging comes from the
+ * library's scratch pool.  Asynchronous on `stream` (the call returns once the chunk offsets,
+ * copied first, have been read): out is complete, and in may be reused, once `stream` has
+ * been synchronised.  Host-buffer calls on one plan are serialised by the library.
+ */
+int tdh_plan_execute_ragged_host(tdh_plan_t plan, const void* in, void* out,
+                                 const int64_t* offsets, int64_t batch, void* stream);
+
+/*
  * tdh_plan_query -- report the plan's rank and size.  K (host, may be NULL) receives the
  * largest rank over the plan's conversion steps; n_max (host, may be NULL) its length.
  */

@@ -25,7 +25,8 @@ EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "t
            "tdh_plan_execute_ragged", "tdh_launch_count", "tdh_plan_execute_host",
            "tdh_plan_schedule_count", "tdh_plan_schedule_info", "tdh_plan_set_schedule",
            "tdh_plan_autotune", "tdh_schedules", "tdh_alloc_stats", "tdh_test_fail_alloc",
-           "tdh_measure_fma_rate", "tdh_plan_status", "tdh_test_tc_stall")
+           "tdh_measure_fma_rate", "tdh_plan_status", "tdh_test_tc_stall",
+           "tdh_plan_execute_ragged_host")
 FLAG_RAGGED = 1
 FLAG_TARGET = 2
 
@@ -77,6 +78,7 @@ def lib():
         L.tdh_plan_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
         L.tdh_test_tc_stall.argtypes = [ctypes.c_int]
         L.tdh_plan_execute_host.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
+        L.tdh_plan_execute_ragged_host.argtypes = [vp, vp, vp, vp, i64, vp]
         L.tdh_plan_schedule_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.tdh_plan_schedule_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.tdh_plan_set_schedule.argtypes = [vp, ctypes.c_int, vp]
@@ -187,11 +189,27 @@ class Plan:
 
     def execute_ragged(self, x, offsets, out=None, stream=None):
         """Convert vectors of different lengths in one call: vector v is
-        x[offsets[v]:offsets[v+1]] (CUDA tensors; offsets int64 with batch + 1 entries, every
-        length <= n).  The plan must have been made with ragged=True."""
+        x[offsets[v]:offsets[v+1]] (offsets int64 with batch + 1 entries, every length <= n).
+        CUDA tensors run on the device; a CPU x with CPU offsets is copied in, converted and
+        copied back in overlapped chunks (synchronise before reading).  The plan must have
+        been made with ragged=True."""
         torch = _torch()
-        if x.dtype != self.dtype or not x.is_contiguous() or x.device.type != "cuda":
-            raise ValueError(f"expected a contiguous CUDA {self.dtype} tensor")
+        if x.dtype != self.dtype or not x.is_contiguous():
+            raise ValueError(f"expected a contiguous {self.dtype} tensor")
+        if x.device.type == "cpu":
+            if offsets.dtype != torch.int64 or offsets.device.type != "cpu" or \
+                    not offsets.is_contiguous():
+                raise ValueError("host x needs contiguous host int64 offsets")
+            res = out if out is not None else torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+            if res.shape != x.shape or res.dtype != x.dtype or res.device.type != "cpu" or \
+                    not res.is_contiguous():
+                raise ValueError("out must be a contiguous host tensor like x")
+            _check(lib().tdh_plan_execute_ragged_host(
+                self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(res.data_ptr()),
+                ctypes.c_void_p(offsets.data_ptr()), offsets.numel() - 1, _stream(stream)))
+            return res
+        if x.device.type != "cuda":
+            raise ValueError(f"expected a contiguous CUDA or host {self.dtype} tensor")
         if offsets.dtype != torch.int64 or offsets.device.type != "cuda":
             raise ValueError("offsets must be a CUDA int64 tensor")
         od = out if out is not None else torch.empty_like(x)

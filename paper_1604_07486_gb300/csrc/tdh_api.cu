@@ -766,6 +766,146 @@ int tdh_plan_execute_ragged(tdh_plan_t plan, const void* in, void* out, const in
                               as_stream(stream), plan->side, plan->ev);
 }
 
+// Ragged batch in host memory: chunks of whole vectors move through the device like
+// run_host's (a sixteenth of the coefficients first and last, the rest in two halves), each
+// chunk converted by the device ragged path with offsets relative to its own staging slot.
+int tdh_plan_execute_ragged_host(tdh_plan_t plan, const void* h_in, void* h_out,
+                                 const int64_t* offsets, int64_t batch, void* stream) {
+    clear_error();
+    if (!plan) {
+        set_error("NULL plan");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch < 0) {
+        set_error("batch must be >= 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch == 0) return TDH_OK;
+    if (!h_in || !h_out || !offsets) {
+        set_error("NULL in/out/offsets");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (!(plan->params.flags & TDH_FLAG_RAGGED) || plan->steps.size() != 1 ||
+        plan->steps[0].rcls.empty()) {
+        set_error("plan was not created with TDH_FLAG_RAGGED");
+        return TDH_ERR_INVALID_ARG;
+    }
+    if (batch > (int64_t)1 << 31) {
+        set_error("ragged batch above 2^31 vectors");
+        return TDH_ERR_UNSUPPORTED;
+    }
+    // the offsets are on the host here, so every length is checked before anything runs
+    if (offsets[0] < 0) {
+        set_error("offsets[0] < 0");
+        return TDH_ERR_INVALID_ARG;
+    }
+    for (int64_t v = 0; v < batch; ++v) {
+        const int64_t len = offsets[v + 1] - offsets[v];
+        if (len < 0 || len > plan->n_max) {
+            set_error("vector %lld: length %lld outside [0, n_max = %lld]", (long long)v,
+                      (long long)len, (long long)plan->n_max);
+            return TDH_ERR_INVALID_ARG;
+        }
+    }
+    const int64_t c0 = offsets[0], total = offsets[batch] - offsets[0];
+    if (total == 0) return TDH_OK;
+    const size_t esz = plan->params.prec == TDH_FP64 ? 8 : 4;
+    const char* hi = static_cast<const char*>(h_in) + esz * (size_t)c0;
+    char* ho = static_cast<char*>(h_out) + esz * (size_t)c0;
+    if (overlaps(hi, ho, esz * (size_t)total)) {
+        set_error("out overlaps in");
+        return TDH_ERR_ALIAS;
+    }
+    // chunk boundaries (vector indices) at coefficient targets: 1/16, 1/2, 15/16 of the total
+    // from 24 MB on, else one chunk; empty chunks dropped
+    std::vector<int64_t> cut{0};
+    if (esz * (size_t)total >= ((size_t)24 << 20)) {
+        for (const int64_t t : {total / 16, total / 2, total - total / 16}) {
+            const int64_t v = std::lower_bound(offsets, offsets + batch + 1, c0 + t) - offsets;
+            if (v > cut.back() && v < batch) cut.push_back(v);
+        }
+    }
+    cut.push_back(batch);
+    const int64_t nchunks = (int64_t)cut.size() - 1;
+    int64_t max_c = 0, max_v = 0;
+    for (int64_t i = 0; i < nchunks; ++i) {
+        max_c = std::max(max_c, offsets[cut[i + 1]] - offsets[cut[i]]);
+        max_v = std::max(max_v, cut[i + 1] - cut[i]);
+    }
+    // chunk-relative offsets of every chunk, uploaded once before the chunks (the host array
+    // may be pageable; an event tells when that copy has read it)
+    std::vector<int64_t> rel((size_t)(batch + nchunks));
+    std::vector<int64_t> first(nchunks);  // index of each chunk's offsets in rel
+    for (int64_t i = 0, k = 0; i < nchunks; ++i) {
+        first[i] = k;
+        for (int64_t v = cut[i]; v <= cut[i + 1]; ++v) rel[(size_t)k++] = offsets[v] - offsets[cut[i]];
+    }
+    const int nslots = nchunks > 1 ? 2 : 1;
+    const size_t data_bytes = (esz * (size_t)max_c + 255) / 256 * 256;
+    const size_t slot_bytes = 2 * data_bytes;  // [in, out]
+    std::lock_guard<std::mutex> lock(plan->host_mu);
+    std::lock_guard<std::mutex> rlock(plan->ragged_mu);
+    cudaStream_t s = as_stream(stream);
+    cudaStream_t cin = plan->hs[0], cout = plan->hs[1];
+    cudaEvent_t* hev = plan->hev;
+    char* dev = nullptr;
+    TDH_TRY(scratch_alloc(reinterpret_cast<void**>(&dev),
+                          slot_bytes * nslots + sizeof(int64_t) * rel.size(), s));
+    auto din = [&](int64_t i) { return dev + slot_bytes * (i % nslots); };
+    auto dout = [&](int64_t i) { return din(i) + data_bytes; };
+    int64_t* doffs = reinterpret_cast<int64_t*>(dev + slot_bytes * nslots);
+    int rc = TDH_OK;
+    cudaEvent_t ev_off = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev_off, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(hev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cin, hev[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, hev[0], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(doffs, rel.data(), sizeof(int64_t) * rel.size(), cudaMemcpyHostToDevice,
+                            cin);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_off, cin);
+    for (int64_t i = 0; e == cudaSuccess && rc == TDH_OK && i < nchunks; ++i) {
+        const int sl = (int)(i % nslots);
+        const int64_t v0 = cut[i], nv = cut[i + 1] - v0;
+        const size_t off = esz * (size_t)(offsets[v0] - c0);
+        const size_t bytes = esz * (size_t)(offsets[cut[i + 1]] - offsets[v0]);
+        // copy in once the conversion of the chunk that last used this slot has read it
+        if (i >= nslots) e = cudaStreamWaitEvent(cin, hev[3 + sl], 0);
+        if (e == cudaSuccess && bytes)
+            e = cudaMemcpyAsync(din(i), hi + off, bytes, cudaMemcpyHostToDevice, cin);
+        if (e == cudaSuccess) e = cudaEventRecord(hev[1 + sl], cin);
+        // convert once the chunk is in and the slot's previous result has been copied out
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, hev[1 + sl], 0);
+        if (e == cudaSuccess && i >= nslots) e = cudaStreamWaitEvent(s, hev[5 + sl], 0);
+        if (e != cudaSuccess) break;
+        rc = exec_launch_ragged(plan->steps[0], plan->params.prec, din(i), dout(i),
+                                doffs + first[i], nv, s, plan->side, plan->ev);
+        if (rc != TDH_OK) break;
+        e = cudaEventRecord(hev[3 + sl], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cout, hev[3 + sl], 0);
+        if (e == cudaSuccess && bytes)
+            e = cudaMemcpyAsync(ho + off, dout(i), bytes, cudaMemcpyDeviceToHost, cout);
+        if (e == cudaSuccess) e = cudaEventRecord(hev[5 + sl], cout);
+    }
+    // join: the caller's stream waits for the last copy out; the slots are freed after it
+    cudaError_t ej = cudaEventRecord(hev[0], cout);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, hev[0], 0);
+    scratch_free(dev, s);
+    // `rel` must outlive the copy that reads it (issued first; normally long complete)
+    if (ev_off) {
+        const cudaError_t es = cudaEventSynchronize(ev_off);
+        if (ej == cudaSuccess) ej = es;
+        cudaEventDestroy(ev_off);
+    }
+    if (rc != TDH_OK) return rc;
+    if (e == cudaSuccess) e = ej;
+    if (e != cudaSuccess) {
+        set_error("ragged host-buffer execute: %s", cudaGetErrorString(e));
+        return TDH_ERR_CUDA;
+    }
+    return TDH_OK;
+}
+
 int tdh_plan_execute(tdh_plan_t plan, const void* in, void* out, int64_t batch, void* stream) {
     return run(plan, in, out, batch, stream, 0);
 }

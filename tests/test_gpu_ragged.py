@@ -161,3 +161,72 @@ def test_ragged_device_checks(tdh):
     with pytest.raises(tdh.TdhError) as e:
         plan.execute_ragged(buf[: 2 * n], offs2, out=buf[: 2 * n])
     assert e.value.code == -7
+
+
+@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+def test_ragged_host_buffers_equal_device(tdh, pinned):
+    """tdh_plan_execute_ragged_host: config 3's batch (4096 vectors, ~39M coefficients, so the
+    chunked pipeline with four chunks of whole vectors) from host memory gives the device
+    ragged path's results bit for bit; so does a small batch (one chunk) with zero-length
+    vectors and a nonzero first offset."""
+    import torch
+    deg = workloads.ragged_degrees(4096, 64, 65536, seed=0)
+    lengths = deg + 1
+    x, offs = workloads.ragged_coefficients(lengths, decay=1.0, seed=0)
+    plan = tdh.Plan("leg2cheb", int(lengths.max()), prec="fp32", tol=1e-7, ragged=True)
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    ot = torch.tensor(offs, dtype=torch.int64, device="cuda")
+    ref = plan.execute_ragged(xt, ot).cpu()
+    hx = torch.tensor(x, dtype=torch.float32)
+    ho = torch.tensor(offs, dtype=torch.int64)
+    if pinned:
+        hx = hx.pin_memory()
+    y = plan.execute_ragged(hx, ho)
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref)
+    assert plan.status() == set()
+    # small batch: one chunk; vectors start at offset 3; two empty vectors
+    lens = np.array([0, 100, 2000, 0, 513])
+    offs2 = np.r_[3, 3 + np.cumsum(lens)].astype(np.int64)
+    x2 = torch.randn(int(offs2[-1]) + 5, dtype=torch.float32)
+    y2 = torch.full_like(x2, 7.0)
+    plan.execute_ragged(x2, torch.tensor(offs2), out=y2)
+    ref2 = torch.full_like(x2, 7.0).cuda()
+    plan.execute_ragged(x2.cuda(), torch.tensor(offs2, device="cuda"), out=ref2)
+    torch.cuda.synchronize()
+    assert torch.equal(y2, ref2.cpu())
+    assert torch.all(y2[:3] == 7.0) and torch.all(y2[int(offs2[-1]):] == 7.0)
+
+
+def test_ragged_host_argument_checks(tdh):
+    """Host offsets are checked before anything runs: decreasing offsets, a negative first
+    offset and a vector longer than n_max are INVALID_ARG; overlapping in and out are ALIAS;
+    a scratch allocation failure is NOMEM and leaves nothing held."""
+    import torch
+    n = 1000
+    plan = tdh.Plan("leg2cheb", n, prec="fp32", ragged=True)
+    x = torch.randn(3 * n, dtype=torch.float32)
+    y = torch.zeros_like(x)
+    for bad in ([0, 500, 400], [-1, 500, 900], [0, 500, 500 + n + 1]):
+        with pytest.raises(tdh.TdhError) as e:
+            plan.execute_ragged(x, torch.tensor(bad, dtype=torch.int64), out=y)
+        assert e.value.code == -1, bad
+    assert torch.all(y == 0)
+    buf = torch.randn(4 * n, dtype=torch.float32)
+    with pytest.raises(tdh.TdhError) as e:
+        plan.execute_ragged(buf[: 2 * n], torch.tensor([0, n, 2 * n]), out=buf[n:3 * n])
+    assert e.value.code == -7
+    _, live0, scr0 = tdh.alloc_stats()
+    tdh.inject_alloc_failure(1)
+    try:
+        with pytest.raises(tdh.TdhError) as e:
+            plan.execute_ragged(x, torch.tensor([0, n, 2 * n, 3 * n]), out=y)
+    finally:
+        tdh.inject_alloc_failure(0)
+    assert e.value.code == -3
+    torch.cuda.synchronize()
+    assert tdh.alloc_stats()[1:] == (live0, scr0)
+    plan.execute_ragged(x, torch.tensor([0, n, 2 * n, 3 * n]), out=y)
+    torch.cuda.synchronize()
+    ref = plan.execute_ragged(x.cuda(), torch.tensor([0, n, 2 * n, 3 * n], device="cuda")).cpu()
+    assert torch.equal(y, ref)
