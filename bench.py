@@ -507,6 +507,12 @@ def main():
     fp32_peak = apeaks["fp32"]
     hbm = peaks.get("hbm_gbs", 6649.7)
     hbm_achieved = 8.0 * coeffs_per_step * args.steps / (total_ms / 1e3) / 1e9
+    # the ceiling of the cluster kernel's cross stage, measured after the timed region
+    dsmem = {"probe_bytes_per_cycle_per_sm": tdh.measure_dsmem_rate(),
+             "cross_stage_bytes_per_rank_term_per_cta": 2 * 3 * (1 << 14) // 4 * 8,
+             "note": "tdh_measure_dsmem_rate: 4-CTA clusters, one 512-thread CTA per SM, "
+                     "16-byte remote accesses; the cross stage moves 96 KB in and 96 KB out "
+                     "per rank term and CTA at C = 4"}
 
     # accuracy of the timed outputs against the oracle (sampled rows)
     err = {}
@@ -603,6 +609,7 @@ def main():
                          "peak_note": f"FP32 FFMA {apeaks['note']}; {apeaks['sms']} SMs"},
             "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
                     "note": "8 algorithmic bytes per coefficient (fp32 in + out); of measured"},
+            "dsmem": dsmem,
             "fp64": fp64,
             "bf16x3": bf,
             "fp32_vs_fp64_n2p20": big,

@@ -307,6 +307,21 @@ int tdh_alloc_stats(int64_t* stats);
 int tdh_measure_fma_rate(int prec, double* tflops, void* stream);
 
 /*
+ * tdh_measure_dsmem_rate -- instrumentation (the paper has no counterpart): the throughput of
+ * distributed shared memory in the access pattern of the float32 cluster kernel's cross stage
+ * (4-CTA clusters, one 512-thread CTA per SM, as many clusters as can be resident, 16-byte
+ * accesses to the other CTAs' shared memory).  bytes_per_cycle (host, 4 doubles) receives
+ * the remote bytes per SM clock cycle per SM for { loads only, stores only, loads and stores
+ * to other places at once (both directions counted) } with every cluster that fits resident,
+ * and { loads only } with a single cluster on the whole device, from each CTA's clock64
+ * cycles (the slowest CTA, best of two timed launches after one untimed).  The cross stage
+ * moves 96 KB in and 96 KB out per rank term and CTA at C = 4, while other clusters are in
+ * other phases.  Synchronous; changes no device setting.
+ * Errors: INVALID_ARG, NOMEM, CUDA.
+ */
+int tdh_measure_dsmem_rate(double* bytes_per_cycle, void* stream);
+
+/*
  * tdh_test_fail_alloc -- failure injection for tests (the paper has no counterpart): the k-th
  * device allocation the library attempts from now on (k >= 1, counting plan memory and
  * execute scratch, all threads) fails on the host as if the device were out of memory: the

@@ -26,7 +26,7 @@ EXPORTS = ("tdh_plan_create", "tdh_plan_execute", "tdh_plan_execute_adjoint", "t
            "tdh_plan_schedule_count", "tdh_plan_schedule_info", "tdh_plan_set_schedule",
            "tdh_plan_autotune", "tdh_schedules", "tdh_alloc_stats", "tdh_test_fail_alloc",
            "tdh_measure_fma_rate", "tdh_plan_status", "tdh_test_tc_stall",
-           "tdh_plan_execute_ragged_host")
+           "tdh_plan_execute_ragged_host", "tdh_measure_dsmem_rate")
 FLAG_RAGGED = 1
 FLAG_TARGET = 2
 
@@ -79,6 +79,7 @@ def lib():
         L.tdh_test_tc_stall.argtypes = [ctypes.c_int]
         L.tdh_plan_execute_host.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
         L.tdh_plan_execute_ragged_host.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.tdh_measure_dsmem_rate.argtypes = [ctypes.POINTER(dbl), vp]
         L.tdh_plan_schedule_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.tdh_plan_schedule_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.tdh_plan_set_schedule.argtypes = [vp, ctypes.c_int, vp]
@@ -323,6 +324,17 @@ def measure_fma_rate(prec, stream=None):
     v = ctypes.c_double()
     _check(lib().tdh_measure_fma_rate(prec, ctypes.byref(v), _stream(stream)))
     return float(v.value)
+
+
+def measure_dsmem_rate(stream=None):
+    """Distributed-shared-memory throughput in the cross stage's access pattern
+    (tdh_measure_dsmem_rate): remote bytes per cycle per SM for loads, stores, and loads with
+    stores (both directions counted) with every cluster resident, and loads with one cluster
+    alone ("loads_one_cluster"), as a dict."""
+    v = (ctypes.c_double * 4)()
+    _check(lib().tdh_measure_dsmem_rate(v, _stream(stream)))
+    return {"loads": float(v[0]), "stores": float(v[1]), "both": float(v[2]),
+            "loads_one_cluster": float(v[3])}
 
 
 def inject_tc_stall(on):
