@@ -560,8 +560,8 @@ def main():
     if not args.no_bf16x3:
         bf = dense_arm_bf16x3(tdh, args, alpha, flush, stream, world, rank, rows)
 
-    # the benchmark spec's precision claim across n = 2^16 .. 2^20: float32 against float64 at
-    # n = 2^20 (multi-pass FFTs), Legendre -> Chebyshev, batch 16
+    # float32 against float64 at the top of the 2^16 .. 2^20 range: n = 2^20 (multi-pass
+    # FFTs), Legendre -> Chebyshev, batch 16
     big = None
     if not args.no_fp64 and not args.no_big:
         big = precision_comparison(tdh, args, flush, stream, world, rank)

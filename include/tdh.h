@@ -62,7 +62,7 @@ extern "C" {
 /* ---------------------------------------------------------------- error codes */
 #define TDH_OK               0
 #define TDH_ERR_INVALID_ARG (-1) /* bad kind, n < 1, parameter out of range, tol <= 0, NULL  */
-#define TDH_ERR_UNSUPPORTED (-2) /* valid request this build does not implement            */
+#define TDH_ERR_UNSUPPORTED (-2) /* valid request the library does not implement          */
 #define TDH_ERR_NOMEM       (-3) /* device or host allocation failed                       */
 #define TDH_ERR_ALIGN       (-4) /* pointer not aligned to 16 bytes                         */
 #define TDH_ERR_TIMEOUT     (-5) /* reserved (device-side waits report through tdh_plan_status) */
@@ -127,7 +127,7 @@ typedef struct {
  * Parameter differences above 4096 return UNSUPPORTED.
  * Synchronous: returns after the plan is complete.  *out receives the handle.
  * Errors: INVALID_ARG (kind, n_max < 1, tol <= 0, NULL out/params, parameters outside the
- * supported case), UNSUPPORTED (a case this build lacks), NOMEM, CUDA.
+ * supported case), UNSUPPORTED (a case the library lacks), NOMEM, CUDA.
  */
 int tdh_plan_create(int kind, int64_t n_max, const tdh_params* params, double tol,
                     tdh_plan_t* out);

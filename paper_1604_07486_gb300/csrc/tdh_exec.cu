@@ -506,7 +506,7 @@ int exec_prepare(Step& st, int prec, cudaStream_t s) {
     int logL = 8;
     while (((int64_t)1 << logL) < 2 * ex.m - 1) ++logL;
     if (!choose_geometry(prec, logL, &ex.g)) {
-        set_error("length %lld needs an FFT of 2^%d points, beyond this build's cluster limit",
+        set_error("length %lld needs an FFT of 2^%d points, beyond the library's cluster limit",
                   (long long)st.n, logL);
         return TDH_ERR_UNSUPPORTED;
     }
