@@ -230,3 +230,22 @@ def test_ragged_host_argument_checks(tdh):
     torch.cuda.synchronize()
     ref = plan.execute_ragged(x.cuda(), torch.tensor([0, n, 2 * n, 3 * n], device="cuda")).cpu()
     assert torch.equal(y, ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_ragged_host_buffers_other_precisions(tdh, prec):
+    """The host-buffer ragged path in float64 and with split-bfloat16 passes: 1000 vectors
+    (~9M coefficients, above 24 MB in either precision, so chunked) equal the device path bit
+    for bit."""
+    import torch
+    lengths = workloads.ragged_degrees(1000, 64, 65536, seed=7) + 1
+    x, offs = workloads.ragged_coefficients(lengths, decay=1.0, seed=7)
+    plan = tdh.Plan("leg2cheb", int(lengths.max()), prec=prec, ragged=True)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ref = plan.execute_ragged(torch.tensor(x, dtype=dt, device="cuda"),
+                              torch.tensor(offs, dtype=torch.int64, device="cuda")).cpu()
+    y = plan.execute_ragged(torch.tensor(x, dtype=dt).pin_memory(),
+                            torch.tensor(offs, dtype=torch.int64))
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref)
+    assert plan.status() == set()
